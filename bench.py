@@ -1,0 +1,438 @@
+#!/usr/bin/env python
+"""ELT-scale SCAO real-time-control benchmark on one GB300 (or N replicas).
+
+One step = one WFS frame through the whole hot path: pixel calibration +
+centre-of-gravity slopes (one kernel) then the split-K MVM fused with the
+leaky integrator (one kernel), on the 74x74-subaperture, 740x740-pixel frame
+with the 4421 x 7944 control matrix (stored FP32 by default).
+
+Timing: every step is bracketed by CUDA events on the launching stream, with an
+event between the two kernels, so the same timed steps give the frame latency
+distribution (p50/p99/p99.9, RMS jitter) and the MVM kernel's duration.  L2 is
+flushed between steps by reading a 512 MiB device buffer (a read leaves only
+clean lines behind, so no write-back lands inside the next step), outside the
+events.  The host
+enqueues each batch of steps behind a device-side sleep so that the GPU never
+waits on the host inside a timed step.  ``e2e`` repeats the measurement through
+the synchronous host-buffer C call (pinned frame in, DM commands out), timed on
+the host clock.
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU oracle
+instead, on the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "ELT-SCAO frame latency p50/p99 µs + RMS jitter; MVM HBM GB/s vs peak"
+FALLBACK_HBM_GBS = 6800.0
+L2_FLUSH_BYTES = 512 << 20
+BATCH = 100
+
+
+def parse_args(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10000)
+    ap.add_argument("--warmup", type=int, default=50)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--store", choices=["f32", "bf16", "fp8"], default="f32")
+    ap.add_argument("--ksplit", type=int, default=0)
+    ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample-s", type=float, default=15.0)
+    ap.add_argument("--reference-budget-s", type=float, default=150.0)
+    ap.add_argument("--oracle-worker", default=None, help=argparse.SUPPRESS)
+    return ap.parse_args(argv)
+
+
+# --------------------------------------------------------------------------- helpers
+def pct(xs, q):
+    s = sorted(xs)
+    if not s:
+        return float("nan")
+    k = (len(s) - 1) * q
+    lo, hi = int(math.floor(k)), int(math.ceil(k))
+    return s[lo] + (s[hi] - s[lo]) * (k - lo)
+
+
+def stats_us(xs):
+    n = len(xs)
+    mean = sum(xs) / n
+    var = sum((x - mean) ** 2 for x in xs) / max(1, n - 1)
+    return {"p50": pct(xs, 0.5), "p99": pct(xs, 0.99), "p999": pct(xs, 0.999), "mean": mean,
+            "rms_jitter": math.sqrt(var), "min": min(xs), "max": max(xs),
+            "peak_to_peak": max(xs) - min(xs)}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def mvm_source_digest():
+    h = hashlib.sha256()
+    with open(os.path.join(ROOT, "paper_1805_07254_gb300", "csrc", "mvm.cu"), "rb") as f:
+        h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(workload):
+    """DRAM bytes per MVM launch from an ncu capture of the current kernel source, else None."""
+    p = os.path.join(ROOT, "profiles", "dram_traffic.txt")
+    if not os.path.exists(p):
+        return None
+    dig = mvm_source_digest()
+    for line in open(p):
+        parts = line.split()
+        if len(parts) == 4 and not line.startswith("#") and parts[0] == "mvm" \
+                and parts[1] == workload and parts[2] == dig:
+            return float(parts[3])
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons, sampled every 50 ms while running."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "50"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.15)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.1)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                rows.append((float(f[1]), float(f[2]), f[5:9]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, _, fl in rows for i, v in enumerate(fl) if v == "Active"})
+        sm = sorted(r[0] for r in rows)
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+# --------------------------------------------------------------------------- oracle (CPU)
+def oracle_worker(path):
+    """Child process: time the FP64 oracle frame by frame (single thread)."""
+    import numpy as np
+    from oracle import pipeline as P
+    d = np.load(path)
+    budget = float(d["budget_s"])
+    max_frames = int(d["max_frames"])
+    loop = P.Loop(d["M"], d["dark"], d["flat"], d["subaps"], int(d["npx"]), float(d["gain"]),
+                  float(d["leak"]))
+    frames = d["frames"]
+    times = []
+    t_start = time.perf_counter()
+    k = 0
+    while k < max_frames and (time.perf_counter() - t_start) < budget:
+        raw = frames[k % frames.shape[0]]
+        t0 = time.perf_counter_ns()
+        loop.step(raw)
+        times.append((time.perf_counter_ns() - t0) / 1e3)
+        k += 1
+    print(json.dumps({"times_us": times}))
+
+
+def run_oracle(cfg, frames, dark, flat, M, budget_s, max_frames):
+    import numpy as np
+    fd, path = tempfile.mkstemp(suffix=".npz")
+    os.close(fd)
+    np.savez(path, M=M, dark=dark, flat=flat, subaps=cfg.subaps, npx=cfg.npx, gain=cfg.gain,
+             leak=cfg.leak, frames=frames, budget_s=budget_s, max_frames=max_frames)
+    env = dict(os.environ)
+    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "NUMEXPR_NUM_THREADS"):
+        env[v] = "1"
+    try:
+        out = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-worker", path],
+                             capture_output=True, text=True, env=env, timeout=budget_s + 300)
+    finally:
+        os.unlink(path)
+    if out.returncode != 0:
+        raise RuntimeError("oracle worker failed: " + out.stderr[-2000:])
+    return json.loads(out.stdout.strip().splitlines()[-1])["times_us"]
+
+
+# --------------------------------------------------------------------------- workload
+def make_workload(n_frames, store):
+    import numpy as np
+    import synth
+    cfg = synth.elt_scao()
+    frames, _ = synth.make_frames(cfg, 0, n_frames)
+    dark, flat = synth.calibration_maps(cfg)
+    M = synth.control_matrix(cfg).numpy()
+    return cfg, frames.numpy(), dark.numpy(), flat.numpy(), np.ascontiguousarray(M)
+
+
+def workload_config(cfg, store, info=None):
+    c = {"workload": f"{cfg.name} ({cfg.frame_side}x{cfg.frame_side} u16 frame, "
+                     f"{cfg.n_valid} subaps x {cfg.npx}x{cfg.npx} px, {cfg.nact}x{cfg.nslopes} "
+                     f"{store} control matrix, leaky integrator)",
+         "frame": f"{cfg.frame_side}x{cfg.frame_side}", "n_valid_subaps": cfg.n_valid,
+         "nslopes": cfg.nslopes, "nact": cfg.nact, "matrix_store": store,
+         "l2": f"flushed between timed steps (read of a {L2_FLUSH_BYTES >> 20} MiB device buffer, outside the events)"}
+    if info:
+        c["ksplit"] = info["ksplit"]
+    return c
+
+
+# --------------------------------------------------------------------------- our arm
+def time_steps(torch, r, d_frames, d_dm, flush, st, n_steps, n_warm):
+    """Per-step (pixel stage us, MVM us, step us) from CUDA events on stream st."""
+    E = torch.cuda.Event
+    nF = len(d_frames)
+    flush_out = torch.empty((), dtype=flush.dtype, device=flush.device)
+
+    def one(i, ev):
+        torch.sum(flush, out=flush_out)
+        if ev:
+            ev[0].record(st)
+        r.centroid_async(d_frames[i % nF], stream=st)
+        if ev:
+            ev[1].record(st)
+        r.reconstruct_async(None, d_dm, stream=st)
+        if ev:
+            ev[2].record(st)
+
+    with torch.cuda.stream(st):
+        for i in range(n_warm):
+            one(i, None)
+        st.synchronize()
+        evs = [(E(enable_timing=True), E(enable_timing=True), E(enable_timing=True))
+               for _ in range(n_steps)]
+        for b0 in range(0, n_steps, BATCH):
+            nb = min(BATCH, n_steps - b0)
+            torch.cuda._sleep(int(2e6))          # device head start while the host enqueues
+            for i in range(b0, b0 + nb):
+                one(i, evs[i])
+        st.synchronize()
+    cog = [evs[i][0].elapsed_time(evs[i][1]) * 1e3 for i in range(n_steps)]
+    mvm = [evs[i][1].elapsed_time(evs[i][2]) * 1e3 for i in range(n_steps)]
+    step = [evs[i][0].elapsed_time(evs[i][2]) * 1e3 for i in range(n_steps)]
+    return cog, mvm, step
+
+
+def ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+
+    from paper_1805_07254_gb300 import Rtc
+
+    n_frames = 16
+    cfg, frames, dark, flat, M = make_workload(n_frames, args.store)
+    hbm_peak, peak_kind = measured_peaks()
+    flush = torch.zeros(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    st = torch.cuda.Stream(device=dev)
+    d_frames = [torch.from_numpy(frames[k]).contiguous().to(dev) for k in range(n_frames)]
+    d_dm = torch.empty(cfg.nact, dtype=torch.float32, device=dev)
+
+    def controller(store):
+        r = Rtc(cfg.nsub, cfg.npx, cfg.nact, obs=cfg.obs, gain=cfg.gain, leak=cfg.leak,
+                device=local, ksplit=args.ksplit)
+        r.load_calib(dark, flat)
+        r.load_cmat(M, store=store)
+        return r
+
+    r = controller(args.store)
+    info = r.info()
+
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local)
+    sampler.start()
+    t_wall = time.perf_counter()
+    cog, mvm, step = time_steps(torch, r, d_frames, d_dm, flush, st, args.steps, args.warmup)
+    t_wall = time.perf_counter() - t_wall
+    clocks = sampler.stop()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+
+    s_step, s_mvm, s_cog = stats_us(step), stats_us(mvm), stats_us(cog)
+    mvm_bytes = info["matrix_bytes"] + 4 * info["nslopes"] + 8 * cfg.nact
+    step_bytes = mvm_bytes + info["frame_bytes"] + info["calib_bytes"]
+    mvm_gbs = mvm_bytes / (s_mvm["mean"] * 1e-6) / 1e9
+
+    # e2e: the synchronous host-buffer C call, pinned frame in, DM commands out
+    pin_frames = [torch.from_numpy(frames[k]).pin_memory() for k in range(n_frames)]
+    pin_dm = torch.empty(cfg.nact, dtype=torch.float32).pin_memory()
+    n_e2e = min(args.steps, 2000)
+    e2e_us = []
+    flush_out = torch.empty((), dtype=torch.float32, device=dev)
+    for i in range(args.warmup + n_e2e):
+        torch.sum(flush, out=flush_out)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter_ns()
+        r.process_frame(pin_frames[i % n_frames], dm_out=pin_dm)
+        t1 = time.perf_counter_ns()
+        if i >= args.warmup:
+            e2e_us.append((t1 - t0) / 1e3)
+    s_e2e = stats_us(e2e_us)
+
+    variants = {}
+    if not args.no_variants:
+        for store in ("f32", "bf16", "fp8"):
+            if store == args.store:
+                continue
+            rv = controller(store)
+            iv = rv.info()
+            c2, m2, s2 = time_steps(torch, rv, d_frames, d_dm, flush, st, min(args.steps, 2000),
+                                    args.warmup)
+            sv, mv = stats_us(s2), stats_us(m2)
+            mb = iv["matrix_bytes"] + 4 * iv["nslopes"] + 8 * cfg.nact
+            variants[store] = {"p50_us": round(sv["p50"], 3), "p99_us": round(sv["p99"], 3),
+                               "rms_jitter_us": round(sv["rms_jitter"], 3),
+                               "mvm_us_mean": round(mv["mean"], 3),
+                               "mvm_hbm_gbs": round(mb / (mv["mean"] * 1e-6) / 1e9, 1),
+                               "mvm_frac_of_peak": round(mb / (mv["mean"] * 1e-6) / 1e9 / hbm_peak, 4)}
+            rv.close()
+
+    # max over ranks (worst replica)
+    value = s_step["p50"]
+    if world > 1:
+        t = torch.tensor([value, s_step["p99"]], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        value = float(t[0])
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        times = run_oracle(cfg, frames[:4], dark, flat, M, args.cpu_sample_s, 400)
+        cpu = {"value": round(pct(times, 0.5), 1), "unit": "us", "cores": 1, "kind": "oracle",
+               "sample": f"{len(times)} ELT frames through the FP64 oracle (single thread, "
+                         f"time-bounded at {args.cpu_sample_s:.0f} s); p50 per frame"}
+
+    traffic = recorded_traffic(f"elt_{args.store}")
+    line = {
+        "metric": METRIC, "value": round(value, 3), "unit": "us", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(s_step["mean"] / 1e3, 6), "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": args.store, "data": "synthetic",
+        "config": workload_config(cfg, args.store, info),
+        "p50_us": round(s_step["p50"], 3), "p99_us": round(s_step["p99"], 3),
+        "p999_us": round(s_step["p999"], 3), "rms_jitter_us": round(s_step["rms_jitter"], 3),
+        "peak_to_peak_us": round(s_step["peak_to_peak"], 3), "mean_us": round(s_step["mean"], 3),
+        "frames_per_s": round(world * 1e6 / s_step["mean"], 1),
+        "stage_us_p50": {"calib_cog": round(s_cog["p50"], 3), "mvm_integrate": round(s_mvm["p50"], 3)},
+        "mvm_hbm_gbs": round(mvm_gbs, 1),
+        "step_hbm_frac": round(step_bytes / (s_step["mean"] * 1e-6) / 1e9 / hbm_peak, 4),
+        "roofline": {"kernel": "mvm_splitk_kernel", "bound": "hbm", "achieved": round(mvm_gbs, 1),
+                     "peak": hbm_peak, "peak_kind": peak_kind, "unit": "GB/s",
+                     "frac": round(mvm_gbs / hbm_peak, 4), "traffic": traffic,
+                     "algorithmic_bytes": mvm_bytes},
+        "e2e": {"value": round(s_e2e["p50"], 3), "unit": "us", "p99_us": round(s_e2e["p99"], 3),
+                "rms_jitter_us": round(s_e2e["rms_jitter"], 3),
+                "h2d_bytes_per_step": info["frame_bytes"], "d2h_bytes_per_step": 4 * cfg.nact,
+                "steps": n_e2e},
+        "gpu_launches": 2 * args.steps,
+        "clocks": clocks,
+        "timed_wall_s_incl_flush": round(t_wall, 3),
+        "variants": variants,
+        "cpu_baseline": cpu,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    r.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+# --------------------------------------------------------------------------- reference arm
+def reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if rank != 0:
+        return
+    cfg, frames, dark, flat, M = make_workload(4, args.store)
+    from oracle import quant as Q
+    Ms = Q.stored_matrix(M, args.store).astype("float32") if args.store != "f32" else M
+    want = args.warmup + args.steps
+    times = run_oracle(cfg, frames, dark, flat, Ms, args.reference_budget_s, want)
+    timed = times[args.warmup:] if len(times) > args.warmup else times
+    s = stats_us(timed)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": round(s["p50"], 1), "unit": "us",
+        "n_gpus": world, "steps": len(timed), "warmup": min(args.warmup, len(times)),
+        "ms_per_step": round(s["mean"] / 1e3, 3), "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": workload_config(cfg, args.store),
+        "p99_us": round(s["p99"], 1), "rms_jitter_us": round(s["rms_jitter"], 1),
+        "cpu_baseline": {"value": round(s["p50"], 1), "unit": "us", "cores": 1, "kind": "oracle",
+                         "sample": f"{len(timed)} of the {args.steps} requested frames "
+                                   f"(time-bounded at {args.reference_budget_s:.0f} s), "
+                                   "single-threaded FP64 oracle"},
+        "e2e": {"value": round(s["p50"], 1), "unit": "us", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse_args()
+    if args.oracle_worker:
+        oracle_worker(args.oracle_worker)
+        return
+    if args.impl == "reference":
+        reference(args)
+    else:
+        ours(args)
+
+
+if __name__ == "__main__":
+    main()

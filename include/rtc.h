@@ -1,0 +1,183 @@
+/*
+ * rtc.h -- C ABI of the GB300 single-conjugate adaptive-optics real-time
+ * controller (librtc.so).
+ *
+ * The library runs, on one CUDA device, the per-frame pipeline of Sec. 2.1 /
+ * Fig. 3 of Jenkins, Basden & Myers (2018):
+ *   (a) pixel calibration   p = (raw - dark) * (1/flat), then a threshold;
+ *   (b) centre-of-gravity   one (x, y) gradient per valid subaperture;
+ *       slope packing       all x gradients first, then all y (Fig. 3 caption);
+ *   (c) reconstruction      d = M s, a dense matrix-vector product (Sec. 1.1.1,
+ *                           memory-bandwidth bound);
+ *   (d) gain                a <- leak * a + g * d  (Sec. 2.1's gain factor,
+ *                           with a leak; leak = 1 gives the plain gain).
+ * The partial products of (c) are summed in a fixed-order tree, the GPU form of
+ * the tree-like partial-vector addition of Sec. 2.3.5.
+ *
+ * Conventions for every entry point:
+ *   - Every function returns an int status: RTC_OK (0) or a negative RTC_E*
+ *     code.  The library never aborts the process.  rtc_last_error() gives a
+ *     human-readable message for the last failure on a handle.
+ *   - Pointers documented as "host" are ordinary (pageable or pinned) host
+ *     memory; "device" pointers are CUDA device memory on the handle's device.
+ *     Input pointers are borrowed for the duration of the call only; the library
+ *     copies what it keeps.  Output buffers are allocated by the caller.
+ *   - All arrays are dense and row-major.  Frames are uint16, (n_wfs, H, W) with
+ *     H = W = nsub * npx.  Slope vectors are float32, per WFS the x block then
+ *     the y block (length 2 * n_valid), WFS after WFS.
+ *   - A handle is not thread-safe: calls on one handle must be serialised by the
+ *     caller.  Different handles are independent.
+ *   - Device-side errors (a failed launch, a fault reported by the runtime)
+ *     return RTC_EDEVICE; a bounded device wait that ran out returns
+ *     RTC_ETIMEDOUT.
+ */
+#ifndef RTC_H
+#define RTC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define RTC_OK          0
+#define RTC_EINVAL     (-1)   /* bad argument or inconsistent sizes */
+#define RTC_ENOMEM     (-2)   /* device or pinned-host allocation failed */
+#define RTC_EDEVICE    (-3)   /* CUDA reported an error */
+#define RTC_ETIMEDOUT  (-4)   /* a bounded device-side wait expired */
+#define RTC_ESTATE     (-5)   /* call not valid in the handle's current state */
+#define RTC_EBUSY      (-6)   /* resource in use (e.g. all serving slots taken) */
+
+/* Storage type of the control matrix.  Accumulation is always FP32. */
+typedef enum rtc_dtype {
+    RTC_F32 = 0,        /* IEEE binary32 */
+    RTC_BF16 = 1,       /* bfloat16, round-to-nearest-even from FP32 */
+    RTC_FP8_E4M3 = 2    /* E4M3 ("fn": bias 7, max 448) codes with one FP32 scale per row */
+} rtc_dtype;
+
+typedef struct rtc_config {
+    int32_t nsub;       /* subapertures across the square grid (e.g. 74) */
+    int32_t npx;        /* pixels per subaperture side (e.g. 10); frame side = nsub*npx */
+    int32_t n_wfs;      /* wavefront-sensor frames per step, stacked (1 for SCAO) */
+    int32_t nact;       /* actuators = rows of the control matrix */
+    float   obs;        /* central obscuration (fraction of the diameter) for the
+                           default subaperture map; see rtc_load_subaps */
+    float   gain;       /* integrator gain g */
+    float   leak;       /* integrator leak */
+    int32_t thr_mode;   /* 0: p < thr -> 0;  1: p -> max(p - thr, 0) */
+    float   thr;        /* threshold in calibrated ADU */
+    int32_t device;     /* CUDA device ordinal */
+    int32_t ksplit;     /* MVM split-K factor; 0 chooses automatically */
+    int32_t reserved;   /* must be 0 */
+} rtc_config;
+
+typedef struct rtc_info {
+    int32_t n_valid;        /* valid subapertures per WFS */
+    int32_t nslopes;        /* 2 * n_valid * n_wfs */
+    int32_t nact;
+    int32_t kpad;           /* matrix row length after padding to a multiple of 16 */
+    int32_t store;          /* rtc_dtype of the loaded matrix, -1 if none */
+    int32_t ksplit;         /* split-K factor in use */
+    int64_t matrix_bytes;   /* algorithmic bytes of the stored matrix (unpadded, incl. scales) */
+    int64_t frame_bytes;    /* n_wfs * H * W * 2 */
+    int64_t calib_bytes;    /* bytes of the per-pixel calibration data read per frame */
+} rtc_info;
+
+typedef struct rtc_handle rtc_handle;
+
+/* Build/version string of the library (static storage; never NULL). */
+const char* rtc_version(void);
+
+/* Message of the last failure on h (or of the last failed rtc_create when h is
+ * NULL).  Static or handle-owned storage valid until the next call on h. */
+const char* rtc_last_error(const rtc_handle* h);
+
+/* Validate cfg and allocate the handle's resident device state.  The default
+ * subaperture map is the set whose centres lie in the annulus
+ * obs*nsub/2 <= r <= nsub/2 (row-major order); the integrator starts at zero.
+ * Errors: RTC_EINVAL (bad geometry or parameters), RTC_ENOMEM, RTC_EDEVICE. */
+int rtc_create(const rtc_config* cfg, rtc_handle** out);
+
+/* Release everything the handle owns.  NULL is accepted. */
+int rtc_destroy(rtc_handle* h);
+
+/* Replace the subaperture map.  rc: host int32 [n_valid][2] of (row, col) grid
+ * positions, strictly increasing in row-major order, each inside the grid.
+ * Invalidates the loaded calibration maps and control matrix (their sizes
+ * depend on n_valid), which must be loaded again.  Errors: RTC_EINVAL. */
+int rtc_load_subaps(rtc_handle* h, const int32_t* rc, int32_t n_valid);
+
+/* Calibration maps for Fig. 3 (a).  dark, flat: host float32 [n_wfs][H][W]
+ * (npix must equal n_wfs*H*W).  The library inverts flat in FP32
+ * (gain = 1.0f/flat, correctly rounded) and keeps, per valid subaperture, the
+ * dark and gain values it needs.  flat entries must be finite and non-zero.
+ * Errors: RTC_EINVAL, RTC_EDEVICE. */
+int rtc_load_calib(rtc_handle* h, const float* dark, const float* flat, int64_t npix);
+
+/* Threshold of Fig. 3 (a): mode 0 zeroes pixels with p < thr; mode 1 maps p to
+ * p - thr when p > thr and to 0 otherwise.  The comparison is made on the FP32
+ * calibrated value.  Errors: RTC_EINVAL. */
+int rtc_set_threshold(rtc_handle* h, int32_t mode, float thr);
+
+/* Control matrix for Fig. 3 (c).  M: host, row-major [nact][nslopes] of type
+ * src (float32, bf16 bits as uint16, or E4M3 codes as uint8).  nact and nslopes
+ * must match the handle.  store selects the device storage: from an RTC_F32
+ * source the library quantises on the device (BF16: round to nearest even;
+ * FP8: per-row scale = max|M_r| / 448, codes = e4m3_rn_satfinite(M_rj / scale),
+ * both divisions in FP32); otherwise store must equal src and, for FP8,
+ * row_scales (host float32 [nact]) must be given.  Rows are padded with zeros to
+ * kpad entries.  Errors: RTC_EINVAL, RTC_ENOMEM, RTC_EDEVICE. */
+int rtc_load_cmat(rtc_handle* h, const void* M, int32_t nact, int32_t nslopes,
+                  int32_t src, int32_t store, const float* row_scales);
+
+/* Integrator parameters of Fig. 3 (d).  Errors: RTC_EINVAL (non-finite). */
+int rtc_set_gain(rtc_handle* h, float gain, float leak);
+
+/* Zero the integrator state (and the predictor's slope history). */
+int rtc_reset(rtc_handle* h);
+
+/* Copy the integrator state (float32 [nact]) to host memory. */
+int rtc_get_dm(rtc_handle* h, float* out);
+
+/* Sizes and byte counts of the loaded configuration. */
+int rtc_get_info(const rtc_handle* h, rtc_info* out);
+
+/* One frame through (a)-(d), synchronously, with host buffers.
+ * frame: host uint16 [n_wfs][H][W]; dm_out: host float32 [nact] receives the
+ * updated integrator state; slopes_out: host float32 [nslopes] or NULL.
+ * The frame is copied to the device, processed on the handle's stream and the
+ * results copied back before the call returns.
+ * Errors: RTC_ESTATE (calibration or matrix not loaded), RTC_EDEVICE. */
+int rtc_process_frame(rtc_handle* h, const uint16_t* frame, float* dm_out, float* slopes_out);
+
+/* The same step on device buffers, enqueued on `stream` (a cudaStream_t; NULL
+ * means the handle's own stream) without synchronising.  d_frame must be 16-byte
+ * aligned.  d_dm_out (float32 [nact]) and d_slopes_out (float32 [nslopes]) may
+ * be NULL.  The integrator state lives on the device; consecutive calls on one
+ * stream form the closed loop.  Errors: RTC_EINVAL, RTC_ESTATE, RTC_EDEVICE. */
+int rtc_process_frame_async(rtc_handle* h, const uint16_t* d_frame, float* d_dm_out,
+                            float* d_slopes_out, void* stream);
+
+/* Stage (a)-(b) alone: calibrate d_frame and write the slope vector into the
+ * handle's resident slope buffer (and into d_slopes_out, float32 [nslopes], when
+ * not NULL), enqueued on `stream` (NULL: own stream).  d_frame must be 16-byte
+ * aligned.  Errors: RTC_EINVAL, RTC_ESTATE, RTC_EDEVICE. */
+int rtc_centroid_async(rtc_handle* h, const uint16_t* d_frame, float* d_slopes_out, void* stream);
+
+/* Stage (c)-(d) alone: d = M s and the integrator update, enqueued on `stream`.
+ * d_slopes: device float32 [nslopes] to reconstruct from, or NULL to use the
+ * resident slope buffer written by the last rtc_centroid_async on this handle.
+ * d_dm_out: device float32 [nact] or NULL.  Errors: RTC_EINVAL, RTC_ESTATE,
+ * RTC_EDEVICE. */
+int rtc_reconstruct_async(rtc_handle* h, const float* d_slopes, float* d_dm_out, void* stream);
+
+/* Block until all work enqueued by the handle on `stream` (NULL: own stream) is
+ * done, and report any device error.  Errors: RTC_EDEVICE. */
+int rtc_synchronize(rtc_handle* h, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RTC_H */

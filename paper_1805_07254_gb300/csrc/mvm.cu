@@ -1,0 +1,284 @@
+// Wavefront reconstruction d = M s (Fig. 3 (c)) fused with the leaky integrator
+// a <- leak * a + g * d (Fig. 3 (d)), and the load-time matrix quantisers.
+//
+// The MVM is bound by the bytes of M it streams from HBM (Sec. 1.1.1), so it
+// runs on CUDA cores as a split-K GEMV:
+//   - block (rb, ks) multiplies rows [4 rb, 4 rb + 4) over the ks-th K slice;
+//     thread t takes the 16-byte chunks t, t+256, ... of the slice for all four
+//     rows, so each s chunk (read through L1) serves four matrix chunks, and the
+//     matrix is read with L1-bypassing non-coherent 16-byte loads;
+//   - stored values are widened to FP32 just before the FMA (BF16 by a shift,
+//     E4M3 by the hardware fp8x2 -> f16x2 conversion), as Sec. 2.3.4 widens
+//     its 16-bit matrix; the FP8 row scale is applied once, after the sum;
+//   - partials are combined in a fixed order: xor butterfly within the warp,
+//     a pairwise tree over the 8 warps, and, when K is split across blocks, a
+//     pairwise tree over the ksplit block partials done by the last block to
+//     finish that row group (arrival counter, self-resetting).  This is the GPU
+//     form of the tree-like partial DM vector addition of Sec. 2.3.5, and the
+//     result does not depend on block scheduling.
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_fp8.h>
+
+#include "rtc_internal.h"
+
+namespace {
+
+__device__ __forceinline__ uint4 ld_stream(const uint4* p) {
+    uint4 v;
+    asm volatile("ld.global.nc.L1::no_allocate.v4.u32 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+                 : "l"(p));
+    return v;
+}
+
+// Elements of the stored type per 16-byte chunk.
+template <int DT> struct Epc;
+template <> struct Epc<RTC_F32> { static constexpr int v = 4; };
+template <> struct Epc<RTC_BF16> { static constexpr int v = 8; };
+template <> struct Epc<RTC_FP8_E4M3> { static constexpr int v = 16; };
+
+__device__ __forceinline__ float bf16_lo(uint32_t u) { return __uint_as_float(u << 16); }
+__device__ __forceinline__ float bf16_hi(uint32_t u) { return __uint_as_float(u & 0xffff0000u); }
+
+__device__ __forceinline__ float2 e4m3x2_to_float2(uint32_t two_codes) {
+    __half2_raw hr = __nv_cvt_fp8x2_to_halfraw2(static_cast<__nv_fp8x2_storage_t>(two_codes),
+                                                __NV_E4M3);
+    return __half22float2(*reinterpret_cast<__half2*>(&hr));
+}
+
+// acc += <chunk m, s values sv[0 .. Epc)>
+template <int DT>
+__device__ __forceinline__ float chunk_dot(float acc, const uint4& m, const float* sv);
+
+template <>
+__device__ __forceinline__ float chunk_dot<RTC_F32>(float acc, const uint4& m, const float* sv) {
+    acc = fmaf(__uint_as_float(m.x), sv[0], acc);
+    acc = fmaf(__uint_as_float(m.y), sv[1], acc);
+    acc = fmaf(__uint_as_float(m.z), sv[2], acc);
+    acc = fmaf(__uint_as_float(m.w), sv[3], acc);
+    return acc;
+}
+
+template <>
+__device__ __forceinline__ float chunk_dot<RTC_BF16>(float acc, const uint4& m, const float* sv) {
+    const uint32_t w[4] = {m.x, m.y, m.z, m.w};
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        acc = fmaf(bf16_lo(w[j]), sv[2 * j], acc);
+        acc = fmaf(bf16_hi(w[j]), sv[2 * j + 1], acc);
+    }
+    return acc;
+}
+
+template <>
+__device__ __forceinline__ float chunk_dot<RTC_FP8_E4M3>(float acc, const uint4& m,
+                                                         const float* sv) {
+    const uint32_t w[4] = {m.x, m.y, m.z, m.w};
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const float2 a = e4m3x2_to_float2(w[j] & 0xffffu);
+        const float2 b = e4m3x2_to_float2(w[j] >> 16);
+        acc = fmaf(a.x, sv[4 * j + 0], acc);
+        acc = fmaf(a.y, sv[4 * j + 1], acc);
+        acc = fmaf(b.x, sv[4 * j + 2], acc);
+        acc = fmaf(b.y, sv[4 * j + 3], acc);
+    }
+    return acc;
+}
+
+template <int DT>
+__device__ __forceinline__ void load_s(const float* __restrict__ s, int chunk, float* sv) {
+    const float4* p = reinterpret_cast<const float4*>(s) + chunk * (Epc<DT>::v / 4);
+#pragma unroll
+    for (int j = 0; j < Epc<DT>::v / 4; ++j) {
+        const float4 v = __ldg(p + j);
+        sv[4 * j + 0] = v.x;
+        sv[4 * j + 1] = v.y;
+        sv[4 * j + 2] = v.z;
+        sv[4 * j + 3] = v.w;
+    }
+}
+
+// Fixed pairwise tree over v[0 .. n): ((v0+v1)+(v2+v3))+...
+__device__ __forceinline__ float tree_sum(float* v, int n) {
+    for (int width = 1; width < n; width <<= 1)
+        for (int i = 0; i + width < n; i += 2 * width) v[i] += v[i + width];
+    return v[0];
+}
+
+template <int DT, int U>
+__global__ void __launch_bounds__(kMvmThreads)
+mvm_splitk_kernel(const uint4* __restrict__ M, int chunks_per_row, int nact,
+                  const float* __restrict__ s, const float* __restrict__ row_scale, int ksplit,
+                  float* __restrict__ partial, unsigned* __restrict__ counter,
+                  float* __restrict__ a, float* __restrict__ dm_out, float gain, float leak) {
+    constexpr int R = kMvmRows;
+    constexpr int NW = kMvmThreads / 32;
+    constexpr int E = Epc<DT>::v;
+    __shared__ float red[R][NW];
+    __shared__ bool last_block;
+
+    const int rb = blockIdx.x;
+    const int ks = blockIdx.y;
+    const int row0 = rb * R;
+    const int c_begin = static_cast<int>((static_cast<long long>(ks) * chunks_per_row) / ksplit);
+    const int c_end = static_cast<int>((static_cast<long long>(ks + 1) * chunks_per_row) / ksplit);
+
+    const uint4* rowp[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int rr = min(row0 + r, nact - 1);   // rows past nact re-read the last row; discarded
+        rowp[r] = M + static_cast<size_t>(rr) * chunks_per_row;
+    }
+
+    float acc[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) acc[r] = 0.f;
+
+    int c = c_begin + threadIdx.x;
+    for (; c + (U - 1) * kMvmThreads < c_end; c += U * kMvmThreads) {
+        uint4 m[U][R];
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+#pragma unroll
+            for (int r = 0; r < R; ++r) m[u][r] = ld_stream(rowp[r] + c + u * kMvmThreads);
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            float sv[E];
+            load_s<DT>(s, c + u * kMvmThreads, sv);
+#pragma unroll
+            for (int r = 0; r < R; ++r) acc[r] = chunk_dot<DT>(acc[r], m[u][r], sv);
+        }
+    }
+    for (; c < c_end; c += kMvmThreads) {
+        uint4 m[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) m[r] = ld_stream(rowp[r] + c);
+        float sv[E];
+        load_s<DT>(s, c, sv);
+#pragma unroll
+        for (int r = 0; r < R; ++r) acc[r] = chunk_dot<DT>(acc[r], m[r], sv);
+    }
+
+    // warp butterfly, then a pairwise tree over the warps
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        float v = acc[r];
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+        if (lane == 0) red[r][warp] = v;
+    }
+    __syncthreads();
+
+    const int t = threadIdx.x;
+    float d = 0.f;
+    if (t < R) {
+        float v[NW];
+#pragma unroll
+        for (int w = 0; w < NW; ++w) v[w] = red[t][w];
+        d = tree_sum(v, NW);
+    }
+
+    if (ksplit > 1) {
+        if (t < R && row0 + t < nact) partial[static_cast<size_t>(ks) * nact + row0 + t] = d;
+        __threadfence();
+        __syncthreads();
+        if (t == 0) last_block = (atomicAdd(counter + rb, 1u) == static_cast<unsigned>(ksplit - 1));
+        __syncthreads();
+        if (!last_block) return;
+        __threadfence();
+        if (t < R && row0 + t < nact) {
+            float v[kMaxKsplit];
+            for (int k = 0; k < ksplit; ++k)
+                v[k] = __ldcg(partial + static_cast<size_t>(k) * nact + row0 + t);
+            d = tree_sum(v, ksplit);
+        }
+        if (t == 0) counter[rb] = 0u;
+    }
+
+    if (t < R && row0 + t < nact) {
+        const int row = row0 + t;
+        if (DT == RTC_FP8_E4M3) d *= row_scale[row];
+        const float an = fmaf(leak, a[row], gain * d);
+        a[row] = an;
+        if (dm_out) dm_out[row] = an;
+    }
+}
+
+template <int DT>
+cudaError_t launch_typed(const rtc_handle* h, const float* d_s, float* d_dm_out, cudaStream_t st) {
+    const int nact = h->cfg.nact;
+    const int cpr = h->kpad / Epc<DT>::v;
+    dim3 grid((nact + kMvmRows - 1) / kMvmRows, h->ksplit);
+    mvm_splitk_kernel<DT, 2><<<grid, kMvmThreads, 0, st>>>(
+        static_cast<const uint4*>(h->d_M), cpr, nact, d_s, h->d_scale, h->ksplit, h->d_partial,
+        h->d_count, h->d_a, d_dm_out, h->gain, h->leak);
+    return cudaGetLastError();
+}
+
+// --- load-time quantisers -----------------------------------------------------
+
+__global__ void pad_bf16_kernel(const float* __restrict__ src, int K, int kpad,
+                                __nv_bfloat16* __restrict__ dst) {
+    const int row = blockIdx.x;
+    for (int j = threadIdx.x; j < kpad; j += blockDim.x) {
+        const float v = j < K ? src[static_cast<size_t>(row) * K + j] : 0.f;
+        dst[static_cast<size_t>(row) * kpad + j] = __float2bfloat16_rn(v);
+    }
+}
+
+__global__ void quant_fp8_kernel(const float* __restrict__ src, int K, int kpad,
+                                 __nv_fp8_storage_t* __restrict__ dst, float* __restrict__ scale) {
+    __shared__ float wmax[32];
+    __shared__ float row_scale;
+    const int row = blockIdx.x;
+    const float* in = src + static_cast<size_t>(row) * K;
+    float m = 0.f;
+    for (int j = threadIdx.x; j < K; j += blockDim.x) m = fmaxf(m, fabsf(in[j]));
+    for (int off = 16; off > 0; off >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, off));
+    if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float mm = 0.f;
+        for (int w = 0; w < static_cast<int>(blockDim.x >> 5); ++w) mm = fmaxf(mm, wmax[w]);
+        row_scale = mm > 0.f ? __fdiv_rn(mm, 448.0f) : 1.0f;
+        scale[row] = row_scale;
+    }
+    __syncthreads();
+    const float sc = row_scale;
+    for (int j = threadIdx.x; j < kpad; j += blockDim.x) {
+        __nv_fp8_storage_t q = 0;
+        if (j < K) q = __nv_cvt_float_to_fp8(__fdiv_rn(in[j], sc), __NV_SATFINITE, __NV_E4M3);
+        dst[static_cast<size_t>(row) * kpad + j] = q;
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_mvm_integrate(const rtc_handle* h, const float* d_s, float* d_dm_out,
+                                 cudaStream_t st) {
+    switch (h->store) {
+        case RTC_F32: return launch_typed<RTC_F32>(h, d_s, d_dm_out, st);
+        case RTC_BF16: return launch_typed<RTC_BF16>(h, d_s, d_dm_out, st);
+        case RTC_FP8_E4M3: return launch_typed<RTC_FP8_E4M3>(h, d_s, d_dm_out, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_quantise(int store, const float* d_src, int nact, int K, int kpad, void* d_dst,
+                            float* d_scale, cudaStream_t st) {
+    if (nact <= 0) return cudaSuccess;
+    if (store == RTC_BF16) {
+        pad_bf16_kernel<<<nact, 256, 0, st>>>(d_src, K, kpad, static_cast<__nv_bfloat16*>(d_dst));
+    } else if (store == RTC_FP8_E4M3) {
+        quant_fp8_kernel<<<nact, 256, 0, st>>>(d_src, K, kpad,
+                                               static_cast<__nv_fp8_storage_t*>(d_dst), d_scale);
+    } else {
+        return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}

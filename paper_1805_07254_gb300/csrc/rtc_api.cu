@@ -1,0 +1,451 @@
+// C-ABI entry points of librtc.so: handle lifecycle, loading of the subaperture
+// map, calibration maps and control matrix, and the per-frame step.
+// Declarations and their contracts are in include/rtc.h.
+
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "rtc_internal.h"
+
+namespace {
+
+thread_local std::string g_create_error;
+
+int fail(rtc_handle* h, int code, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (h) h->err = buf; else g_create_error = buf;
+    return code;
+}
+
+// Makes the handle's device current for the scope and restores the caller's.
+struct DeviceScope {
+    int prev = -1;
+    explicit DeviceScope(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceScope() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+#define RTC_CUDA(h, call)                                                                  \
+    do {                                                                                   \
+        cudaError_t e_ = (call);                                                           \
+        if (e_ != cudaSuccess)                                                             \
+            return fail((h), RTC_EDEVICE, "%s failed: %s", #call, cudaGetErrorString(e_)); \
+    } while (0)
+
+template <typename T>
+void free_dev(T*& p) {
+    if (p) cudaFree(p);
+    p = nullptr;
+}
+
+int dtype_size(int dt) {
+    switch (dt) {
+        case RTC_F32: return 4;
+        case RTC_BF16: return 2;
+        case RTC_FP8_E4M3: return 1;
+        default: return 0;
+    }
+}
+
+// Default map: subaperture centres inside the annulus obs*n/2 <= r <= n/2,
+// radii in subaperture pitches from the grid centre, row-major order.
+std::vector<int32_t> default_subaps(int n, float obs) {
+    std::vector<int32_t> rc;
+    const double ro2 = (n / 2.0) * (n / 2.0);
+    const double ri = static_cast<double>(obs) * n / 2.0;
+    const double ri2 = ri * ri;
+    for (int r = 0; r < n; ++r)
+        for (int c = 0; c < n; ++c) {
+            const double y = r + 0.5 - n / 2.0, x = c + 0.5 - n / 2.0;
+            const double d2 = x * x + y * y;
+            if (d2 <= ro2 && d2 >= ri2) {
+                rc.push_back(r);
+                rc.push_back(c);
+            }
+        }
+    return rc;
+}
+
+int choose_ksplit(const rtc_handle* h) {
+    if (h->cfg.ksplit > 0) return std::min(h->cfg.ksplit, kMaxKsplit);
+    return 1;
+}
+
+// (Re)build everything whose size depends on the subaperture map.
+int apply_subaps(rtc_handle* h, const std::vector<int32_t>& rc) {
+    const int n = h->cfg.nsub;
+    const int nv = static_cast<int>(rc.size() / 2);
+    for (int i = 0; i < nv; ++i) {
+        const int r = rc[2 * i], c = rc[2 * i + 1];
+        if (r < 0 || r >= n || c < 0 || c >= n)
+            return fail(h, RTC_EINVAL, "subap %d at (%d,%d) lies outside the %dx%d grid", i, r, c, n, n);
+        if (i > 0) {
+            const long prev = static_cast<long>(rc[2 * i - 2]) * n + rc[2 * i - 1];
+            if (static_cast<long>(r) * n + c <= prev)
+                return fail(h, RTC_EINVAL, "subap map must be strictly increasing in row-major order (entry %d)", i);
+        }
+    }
+    std::vector<int32_t> bands, cols(nv);
+    for (int i = 0; i < nv; ++i) {
+        cols[i] = rc[2 * i + 1];
+        if (i == 0 || rc[2 * i] != rc[2 * i - 2]) {
+            bands.push_back(rc[2 * i]);
+            bands.push_back(i);
+            bands.push_back(0);
+        }
+        bands.back() += 1;
+    }
+    free_dev(h->d_band);
+    free_dev(h->d_subcol);
+    free_dev(h->d_dark);
+    free_dev(h->d_gainmap);
+    free_dev(h->d_M);
+    free_dev(h->d_scale);
+    free_dev(h->d_s);
+    h->rc = rc;
+    h->n_valid = nv;
+    h->nslopes = 2 * nv * h->cfg.n_wfs;
+    h->kpad = (h->nslopes + 15) / 16 * 16;
+    h->nbands = static_cast<int>(bands.size() / 3);
+    h->store = -1;
+    h->calib_loaded = false;
+    if (nv > 0) {
+        RTC_CUDA(h, cudaMalloc(&h->d_band, bands.size() * sizeof(int32_t)));
+        RTC_CUDA(h, cudaMemcpy(h->d_band, bands.data(), bands.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+        RTC_CUDA(h, cudaMalloc(&h->d_subcol, nv * sizeof(int32_t)));
+        RTC_CUDA(h, cudaMemcpy(h->d_subcol, cols.data(), nv * sizeof(int32_t), cudaMemcpyHostToDevice));
+    }
+    RTC_CUDA(h, cudaMalloc(&h->d_s, std::max(h->kpad, 16) * sizeof(float)));
+    RTC_CUDA(h, cudaMemset(h->d_s, 0, std::max(h->kpad, 16) * sizeof(float)));
+    return RTC_OK;
+}
+
+int check_ready(rtc_handle* h) {
+    if (!h) return RTC_EINVAL;
+    if (!h->calib_loaded) return fail(h, RTC_ESTATE, "calibration maps not loaded");
+    if (h->store < 0) return fail(h, RTC_ESTATE, "control matrix not loaded");
+    return RTC_OK;
+}
+
+int enqueue_step(rtc_handle* h, const uint16_t* d_frame, float* d_dm_out, float* d_slopes_out,
+                 cudaStream_t st) {
+    RTC_CUDA(h, launch_calib_cog(h, d_frame, h->d_s, st));
+    RTC_CUDA(h, launch_mvm_integrate(h, h->d_s, d_dm_out, st));
+    if (d_slopes_out)
+        RTC_CUDA(h, cudaMemcpyAsync(d_slopes_out, h->d_s, h->nslopes * sizeof(float),
+                                    cudaMemcpyDeviceToDevice, st));
+    return RTC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* rtc_version(void) { return "librtc 0.1 (sm_103a)"; }
+
+const char* rtc_last_error(const rtc_handle* h) {
+    return h ? h->err.c_str() : g_create_error.c_str();
+}
+
+int rtc_create(const rtc_config* cfg, rtc_handle** out) {
+    if (!cfg || !out) return fail(nullptr, RTC_EINVAL, "cfg and out must be non-NULL");
+    *out = nullptr;
+    const rtc_config& c = *cfg;
+    if (c.nsub <= 0 || c.npx <= 0 || c.n_wfs <= 0 || c.nact <= 0)
+        return fail(nullptr, RTC_EINVAL, "nsub, npx, n_wfs and nact must be positive");
+    if (static_cast<long long>(c.nsub) * c.npx > 16384)
+        return fail(nullptr, RTC_EINVAL, "frame side %lld exceeds 16384", (long long)c.nsub * c.npx);
+    if (!(c.obs >= 0.f && c.obs < 1.f)) return fail(nullptr, RTC_EINVAL, "obs must be in [0, 1)");
+    if (!isfinite(c.gain) || !isfinite(c.leak) || !isfinite(c.thr))
+        return fail(nullptr, RTC_EINVAL, "gain, leak and thr must be finite");
+    if (c.thr_mode != 0 && c.thr_mode != 1) return fail(nullptr, RTC_EINVAL, "thr_mode must be 0 or 1");
+    if (c.ksplit < 0) return fail(nullptr, RTC_EINVAL, "ksplit must be >= 0");
+    if (c.reserved != 0) return fail(nullptr, RTC_EINVAL, "reserved must be 0");
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || c.device < 0 || c.device >= ndev)
+        return fail(nullptr, RTC_EINVAL, "device %d not available", c.device);
+
+    rtc_handle* h = new rtc_handle();
+    h->cfg = c;
+    h->side = c.nsub * c.npx;
+    h->gain = c.gain;
+    h->leak = c.leak;
+    h->thr_mode = c.thr_mode;
+    h->thr = c.thr;
+    h->ksplit = choose_ksplit(h);
+    DeviceScope ds(c.device);
+    int rcode = RTC_OK;
+    const size_t smem = static_cast<size_t>(c.npx) * h->side * sizeof(uint16_t) + 16;
+    int smem_optin = 0;
+    cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c.device);
+    if (smem > static_cast<size_t>(smem_optin)) {
+        rcode = fail(nullptr, RTC_EINVAL, "a band of npx*side pixels (%zu B) exceeds shared memory", smem);
+    } else if (calib_cog_configure(static_cast<size_t>(smem_optin)) != cudaSuccess) {
+        rcode = fail(nullptr, RTC_EDEVICE, "cannot configure the pixel-stage shared memory");
+    } else if (cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking) != cudaSuccess) {
+        rcode = fail(nullptr, RTC_EDEVICE, "cudaStreamCreate failed");
+    } else {
+        const size_t nrb = (c.nact + kMvmRows - 1) / kMvmRows;
+        const size_t frame_elems = static_cast<size_t>(c.n_wfs) * h->side * h->side;
+        if (cudaMalloc(&h->d_a, c.nact * sizeof(float)) != cudaSuccess ||
+            cudaMalloc(&h->d_partial, static_cast<size_t>(kMaxKsplit) * c.nact * sizeof(float)) != cudaSuccess ||
+            cudaMalloc(&h->d_count, nrb * sizeof(unsigned)) != cudaSuccess ||
+            cudaMalloc(&h->d_frame, frame_elems * sizeof(uint16_t)) != cudaSuccess) {
+            rcode = fail(nullptr, RTC_ENOMEM, "device allocation failed");
+        } else if (cudaMemset(h->d_a, 0, c.nact * sizeof(float)) != cudaSuccess ||
+                   cudaMemset(h->d_count, 0, nrb * sizeof(unsigned)) != cudaSuccess) {
+            rcode = fail(nullptr, RTC_EDEVICE, "cudaMemset failed");
+        } else {
+            rcode = apply_subaps(h, default_subaps(c.nsub, c.obs));
+            if (rcode != RTC_OK) g_create_error = h->err;
+        }
+    }
+    if (rcode != RTC_OK) {
+        rtc_destroy(h);
+        return rcode;
+    }
+    *out = h;
+    return RTC_OK;
+}
+
+int rtc_destroy(rtc_handle* h) {
+    if (!h) return RTC_OK;
+    DeviceScope ds(h->cfg.device);
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    free_dev(h->d_band);
+    free_dev(h->d_subcol);
+    free_dev(h->d_dark);
+    free_dev(h->d_gainmap);
+    free_dev(h->d_M);
+    free_dev(h->d_scale);
+    free_dev(h->d_s);
+    free_dev(h->d_a);
+    free_dev(h->d_partial);
+    free_dev(h->d_count);
+    free_dev(h->d_frame);
+    if (h->stream) cudaStreamDestroy(h->stream);
+    delete h;
+    return RTC_OK;
+}
+
+int rtc_load_subaps(rtc_handle* h, const int32_t* rc, int32_t n_valid) {
+    if (!h) return RTC_EINVAL;
+    if (n_valid < 0 || (n_valid > 0 && !rc)) return fail(h, RTC_EINVAL, "bad subap map");
+    DeviceScope ds(h->cfg.device);
+    RTC_CUDA(h, cudaStreamSynchronize(h->stream));
+    std::vector<int32_t> v(rc, rc + 2 * static_cast<size_t>(n_valid));
+    return apply_subaps(h, v);
+}
+
+int rtc_load_calib(rtc_handle* h, const float* dark, const float* flat, int64_t npix) {
+    if (!h) return RTC_EINVAL;
+    const int side = h->side, npx = h->cfg.npx, nw = h->cfg.n_wfs, nv = h->n_valid;
+    const int64_t want = static_cast<int64_t>(nw) * side * side;
+    if (!dark || !flat || npix != want)
+        return fail(h, RTC_EINVAL, "calibration maps must hold n_wfs*H*W = %lld pixels", (long long)want);
+    const int npp = npx * npx;
+    std::vector<float> dk(static_cast<size_t>(nw) * nv * npp), gk(dk.size());
+    for (int w = 0; w < nw; ++w)
+        for (int i = 0; i < nv; ++i) {
+            const int r = h->rc[2 * i], c = h->rc[2 * i + 1];
+            for (int y = 0; y < npx; ++y)
+                for (int x = 0; x < npx; ++x) {
+                    const size_t src = static_cast<size_t>(w) * side * side +
+                                       static_cast<size_t>(r * npx + y) * side + (c * npx + x);
+                    const size_t dst = (static_cast<size_t>(w) * nv + i) * npp + y * npx + x;
+                    const float f = flat[src];
+                    if (!(f != 0.f) || !isfinite(f) || !isfinite(dark[src]))
+                        return fail(h, RTC_EINVAL, "flat must be finite and non-zero, dark finite (pixel %zu)", src);
+                    dk[dst] = dark[src];
+                    gk[dst] = 1.0f / f;
+                }
+        }
+    DeviceScope ds(h->cfg.device);
+    RTC_CUDA(h, cudaStreamSynchronize(h->stream));
+    free_dev(h->d_dark);
+    free_dev(h->d_gainmap);
+    h->calib_loaded = false;
+    if (!dk.empty()) {
+        RTC_CUDA(h, cudaMalloc(&h->d_dark, dk.size() * sizeof(float)));
+        RTC_CUDA(h, cudaMalloc(&h->d_gainmap, gk.size() * sizeof(float)));
+        RTC_CUDA(h, cudaMemcpy(h->d_dark, dk.data(), dk.size() * sizeof(float), cudaMemcpyHostToDevice));
+        RTC_CUDA(h, cudaMemcpy(h->d_gainmap, gk.data(), gk.size() * sizeof(float), cudaMemcpyHostToDevice));
+    }
+    h->calib_loaded = true;
+    return RTC_OK;
+}
+
+int rtc_set_threshold(rtc_handle* h, int32_t mode, float thr) {
+    if (!h) return RTC_EINVAL;
+    if ((mode != 0 && mode != 1) || !isfinite(thr)) return fail(h, RTC_EINVAL, "bad threshold");
+    h->thr_mode = mode;
+    h->thr = thr;
+    return RTC_OK;
+}
+
+int rtc_load_cmat(rtc_handle* h, const void* M, int32_t nact, int32_t nslopes, int32_t src,
+                  int32_t store, const float* row_scales) {
+    if (!h) return RTC_EINVAL;
+    if (!M) return fail(h, RTC_EINVAL, "M is NULL");
+    if (nact != h->cfg.nact || nslopes != h->nslopes)
+        return fail(h, RTC_EINVAL, "matrix is %dx%d, handle expects %dx%d", nact, nslopes, h->cfg.nact, h->nslopes);
+    if (dtype_size(src) == 0 || dtype_size(store) == 0) return fail(h, RTC_EINVAL, "unknown dtype");
+    if (src != RTC_F32 && src != store) return fail(h, RTC_EINVAL, "only an FP32 source can be converted");
+    if (src == RTC_FP8_E4M3 && !row_scales) return fail(h, RTC_EINVAL, "FP8 source needs row_scales");
+    DeviceScope ds(h->cfg.device);
+    RTC_CUDA(h, cudaStreamSynchronize(h->stream));
+    free_dev(h->d_M);
+    free_dev(h->d_scale);
+    h->store = -1;
+    const int esz = dtype_size(store);
+    const size_t bytes = static_cast<size_t>(nact) * h->kpad * esz;
+    RTC_CUDA(h, cudaMalloc(&h->d_scale, nact * sizeof(float)));
+    if (bytes == 0) {            // no valid subapertures: an empty matrix, d = 0
+        h->store = store;
+        return RTC_OK;
+    }
+    if (cudaMalloc(&h->d_M, bytes) != cudaSuccess) {
+        h->d_M = nullptr;
+        return fail(h, RTC_ENOMEM, "cannot allocate %zu bytes for the matrix", bytes);
+    }
+    RTC_CUDA(h, cudaMemset(h->d_M, 0, bytes));
+    if (src == store) {
+        RTC_CUDA(h, cudaMemcpy2D(h->d_M, static_cast<size_t>(h->kpad) * esz, M,
+                                 static_cast<size_t>(nslopes) * esz, static_cast<size_t>(nslopes) * esz,
+                                 nact, cudaMemcpyHostToDevice));
+        if (store == RTC_FP8_E4M3)
+            RTC_CUDA(h, cudaMemcpy(h->d_scale, row_scales, nact * sizeof(float), cudaMemcpyHostToDevice));
+    } else {
+        float* staging = nullptr;
+        const size_t sbytes = static_cast<size_t>(nact) * nslopes * sizeof(float);
+        if (cudaMalloc(&staging, sbytes) != cudaSuccess)
+            return fail(h, RTC_ENOMEM, "cannot allocate %zu bytes of staging", sbytes);
+        cudaError_t e = cudaMemcpy(staging, M, sbytes, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = launch_quantise(store, staging, nact, nslopes, h->kpad, h->d_M, h->d_scale, h->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        cudaFree(staging);
+        if (e != cudaSuccess) return fail(h, RTC_EDEVICE, "matrix conversion failed: %s", cudaGetErrorString(e));
+    }
+    h->store = store;
+    return RTC_OK;
+}
+
+int rtc_set_gain(rtc_handle* h, float gain, float leak) {
+    if (!h) return RTC_EINVAL;
+    if (!isfinite(gain) || !isfinite(leak)) return fail(h, RTC_EINVAL, "gain and leak must be finite");
+    h->gain = gain;
+    h->leak = leak;
+    return RTC_OK;
+}
+
+int rtc_reset(rtc_handle* h) {
+    if (!h) return RTC_EINVAL;
+    DeviceScope ds(h->cfg.device);
+    RTC_CUDA(h, cudaMemsetAsync(h->d_a, 0, h->cfg.nact * sizeof(float), h->stream));
+    RTC_CUDA(h, cudaStreamSynchronize(h->stream));
+    return RTC_OK;
+}
+
+int rtc_get_dm(rtc_handle* h, float* out) {
+    if (!h || !out) return h ? fail(h, RTC_EINVAL, "out is NULL") : RTC_EINVAL;
+    DeviceScope ds(h->cfg.device);
+    RTC_CUDA(h, cudaMemcpyAsync(out, h->d_a, h->cfg.nact * sizeof(float), cudaMemcpyDeviceToHost, h->stream));
+    RTC_CUDA(h, cudaStreamSynchronize(h->stream));
+    return RTC_OK;
+}
+
+int rtc_get_info(const rtc_handle* h, rtc_info* out) {
+    if (!h || !out) return RTC_EINVAL;
+    out->n_valid = h->n_valid;
+    out->nslopes = h->nslopes;
+    out->nact = h->cfg.nact;
+    out->kpad = h->kpad;
+    out->store = h->store;
+    out->ksplit = h->ksplit;
+    const int64_t entries = static_cast<int64_t>(h->cfg.nact) * h->nslopes;
+    int64_t mb = 0;
+    if (h->store >= 0) mb = entries * dtype_size(h->store) + (h->store == RTC_FP8_E4M3 ? 4LL * h->cfg.nact : 0);
+    out->matrix_bytes = mb;
+    out->frame_bytes = static_cast<int64_t>(h->cfg.n_wfs) * h->side * h->side * 2;
+    out->calib_bytes = 2LL * 4 * h->cfg.n_wfs * h->n_valid * h->cfg.npx * h->cfg.npx;
+    return RTC_OK;
+}
+
+int rtc_process_frame(rtc_handle* h, const uint16_t* frame, float* dm_out, float* slopes_out) {
+    int rc = check_ready(h);
+    if (rc != RTC_OK) return rc;
+    if (!frame || !dm_out) return fail(h, RTC_EINVAL, "frame and dm_out must be non-NULL");
+    DeviceScope ds(h->cfg.device);
+    const size_t fbytes = static_cast<size_t>(h->cfg.n_wfs) * h->side * h->side * sizeof(uint16_t);
+    RTC_CUDA(h, cudaMemcpyAsync(h->d_frame, frame, fbytes, cudaMemcpyHostToDevice, h->stream));
+    rc = enqueue_step(h, h->d_frame, nullptr, nullptr, h->stream);
+    if (rc != RTC_OK) return rc;
+    RTC_CUDA(h, cudaMemcpyAsync(dm_out, h->d_a, h->cfg.nact * sizeof(float), cudaMemcpyDeviceToHost, h->stream));
+    if (slopes_out)
+        RTC_CUDA(h, cudaMemcpyAsync(slopes_out, h->d_s, h->nslopes * sizeof(float), cudaMemcpyDeviceToHost, h->stream));
+    RTC_CUDA(h, cudaStreamSynchronize(h->stream));
+    return RTC_OK;
+}
+
+int rtc_process_frame_async(rtc_handle* h, const uint16_t* d_frame, float* d_dm_out,
+                            float* d_slopes_out, void* stream) {
+    int rc = check_ready(h);
+    if (rc != RTC_OK) return rc;
+    if (!d_frame) return fail(h, RTC_EINVAL, "d_frame is NULL");
+    if (reinterpret_cast<uintptr_t>(d_frame) & 15) return fail(h, RTC_EINVAL, "d_frame must be 16-byte aligned");
+    DeviceScope ds(h->cfg.device);
+    cudaStream_t st = stream ? static_cast<cudaStream_t>(stream) : h->stream;
+    return enqueue_step(h, d_frame, d_dm_out, d_slopes_out, st);
+}
+
+int rtc_centroid_async(rtc_handle* h, const uint16_t* d_frame, float* d_slopes_out, void* stream) {
+    if (!h) return RTC_EINVAL;
+    if (!h->calib_loaded) return fail(h, RTC_ESTATE, "calibration maps not loaded");
+    if (!d_frame) return fail(h, RTC_EINVAL, "d_frame is NULL");
+    if (reinterpret_cast<uintptr_t>(d_frame) & 15) return fail(h, RTC_EINVAL, "d_frame must be 16-byte aligned");
+    DeviceScope ds(h->cfg.device);
+    cudaStream_t st = stream ? static_cast<cudaStream_t>(stream) : h->stream;
+    RTC_CUDA(h, launch_calib_cog(h, d_frame, h->d_s, st));
+    if (d_slopes_out)
+        RTC_CUDA(h, cudaMemcpyAsync(d_slopes_out, h->d_s, h->nslopes * sizeof(float),
+                                    cudaMemcpyDeviceToDevice, st));
+    return RTC_OK;
+}
+
+int rtc_reconstruct_async(rtc_handle* h, const float* d_slopes, float* d_dm_out, void* stream) {
+    if (!h) return RTC_EINVAL;
+    if (h->store < 0) return fail(h, RTC_ESTATE, "control matrix not loaded");
+    DeviceScope ds(h->cfg.device);
+    cudaStream_t st = stream ? static_cast<cudaStream_t>(stream) : h->stream;
+    if (d_slopes && d_slopes != h->d_s)
+        RTC_CUDA(h, cudaMemcpyAsync(h->d_s, d_slopes, h->nslopes * sizeof(float),
+                                    cudaMemcpyDeviceToDevice, st));
+    RTC_CUDA(h, launch_mvm_integrate(h, h->d_s, d_dm_out, st));
+    return RTC_OK;
+}
+
+int rtc_synchronize(rtc_handle* h, void* stream) {
+    if (!h) return RTC_EINVAL;
+    DeviceScope ds(h->cfg.device);
+    cudaStream_t st = stream ? static_cast<cudaStream_t>(stream) : h->stream;
+    RTC_CUDA(h, cudaStreamSynchronize(st));
+    RTC_CUDA(h, cudaGetLastError());
+    return RTC_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,69 @@
+// Internal state and kernel launchers shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "rtc.h"
+
+// Threads per block of the pixel stage and of the reconstruction stage.
+constexpr int kCalibThreads = 256;
+constexpr int kMvmThreads = 256;
+// Matrix rows handled together by one reconstruction block.
+constexpr int kMvmRows = 4;
+// Largest split-K factor (partials per actuator summed by the fixed-order tree).
+constexpr int kMaxKsplit = 32;
+
+struct rtc_handle {
+    rtc_config cfg{};
+    int side = 0;               // frame side in pixels (nsub * npx)
+    int n_valid = 0;            // valid subapertures per WFS
+    int nslopes = 0;            // 2 * n_valid * n_wfs
+    int kpad = 0;               // padded matrix row length (elements)
+    int store = -1;             // rtc_dtype of the resident matrix, -1 when none
+    int ksplit = 1;
+    int nbands = 0;             // subaperture rows holding at least one valid subap
+    float gain = 0.f, leak = 1.f;
+    int thr_mode = 0;
+    float thr = 0.f;
+    bool calib_loaded = false;
+
+    cudaStream_t stream = nullptr;
+
+    std::vector<int32_t> rc;    // host copy of the subaperture map (row, col) pairs
+
+    // device buffers (owned)
+    int32_t* d_band = nullptr;      // [nbands][3]: grid row, first valid index, count
+    int32_t* d_subcol = nullptr;    // [n_valid] grid column of each valid subap
+    float* d_dark = nullptr;        // [n_wfs][n_valid][npx*npx] dark, subap-major
+    float* d_gainmap = nullptr;     // [n_wfs][n_valid][npx*npx] 1/flat, subap-major
+    void* d_M = nullptr;            // [nact][kpad] in the stored type
+    float* d_scale = nullptr;       // [nact] FP8 row scales
+    float* d_s = nullptr;           // [kpad] slope vector, zero padded
+    float* d_a = nullptr;           // [nact] integrator state
+    float* d_partial = nullptr;     // [kMaxKsplit][nact] split-K partial products (scratch)
+    unsigned* d_count = nullptr;    // [ceil(nact/kMvmRows)] arrival counters (scratch, self-resetting)
+    uint16_t* d_frame = nullptr;    // [n_wfs][side][side] staging for host frames
+
+    std::string err;
+};
+
+// Pixel calibration + centre of gravity + slope packing for every valid
+// subaperture of every WFS frame.  Writes s[0 .. nslopes).
+cudaError_t launch_calib_cog(const rtc_handle* h, const uint16_t* d_frame, float* d_s,
+                             cudaStream_t st);
+
+// Split-K MVM with the fused fixed-order partial tree and leaky integrator.
+cudaError_t launch_mvm_integrate(const rtc_handle* h, const float* d_s, float* d_dm_out,
+                                 cudaStream_t st);
+
+// Convert an FP32 device matrix [nact][K] into the stored layout [nact][kpad].
+cudaError_t launch_quantise(int store, const float* d_src, int nact, int K, int kpad,
+                            void* d_dst, float* d_scale, cudaStream_t st);
+
+// Smallest dynamic shared memory the pixel stage needs for this geometry.
+size_t calib_cog_smem_bytes(const rtc_handle* h);
+cudaError_t calib_cog_configure(size_t smem_bytes);

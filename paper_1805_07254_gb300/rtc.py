@@ -1,0 +1,231 @@
+"""ctypes binding of librtc.so (include/rtc.h) -- argument marshalling only.
+
+Every computation happens in the library's CUDA kernels; this module converts
+numpy arrays / torch tensors to pointers, checks status codes and raises
+``RtcError``.  If the library has not been built the import of ``Rtc`` fails
+loudly: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "librtc.so")
+
+RTC_OK, RTC_EINVAL, RTC_ENOMEM, RTC_EDEVICE, RTC_ETIMEDOUT, RTC_ESTATE, RTC_EBUSY = 0, -1, -2, -3, -4, -5, -6
+DTYPES = {"f32": 0, "bf16": 1, "fp8": 2}
+_ERRNAMES = {0: "RTC_OK", -1: "RTC_EINVAL", -2: "RTC_ENOMEM", -3: "RTC_EDEVICE",
+             -4: "RTC_ETIMEDOUT", -5: "RTC_ESTATE", -6: "RTC_EBUSY"}
+
+
+class RtcConfig(C.Structure):
+    _fields_ = [("nsub", C.c_int32), ("npx", C.c_int32), ("n_wfs", C.c_int32), ("nact", C.c_int32),
+                ("obs", C.c_float), ("gain", C.c_float), ("leak", C.c_float),
+                ("thr_mode", C.c_int32), ("thr", C.c_float), ("device", C.c_int32),
+                ("ksplit", C.c_int32), ("reserved", C.c_int32)]
+
+
+class RtcInfo(C.Structure):
+    _fields_ = [("n_valid", C.c_int32), ("nslopes", C.c_int32), ("nact", C.c_int32),
+                ("kpad", C.c_int32), ("store", C.c_int32), ("ksplit", C.c_int32),
+                ("matrix_bytes", C.c_int64), ("frame_bytes", C.c_int64), ("calib_bytes", C.c_int64)]
+
+
+_P = C.c_void_p
+_I = C.c_int
+# name -> (restype, argtypes); mirrors include/rtc.h
+SIGNATURES = {
+    "rtc_version": (C.c_char_p, []),
+    "rtc_last_error": (C.c_char_p, [_P]),
+    "rtc_create": (_I, [C.POINTER(RtcConfig), C.POINTER(_P)]),
+    "rtc_destroy": (_I, [_P]),
+    "rtc_load_subaps": (_I, [_P, _P, C.c_int32]),
+    "rtc_load_calib": (_I, [_P, _P, _P, C.c_int64]),
+    "rtc_set_threshold": (_I, [_P, C.c_int32, C.c_float]),
+    "rtc_load_cmat": (_I, [_P, _P, C.c_int32, C.c_int32, C.c_int32, C.c_int32, _P]),
+    "rtc_set_gain": (_I, [_P, C.c_float, C.c_float]),
+    "rtc_reset": (_I, [_P]),
+    "rtc_get_dm": (_I, [_P, _P]),
+    "rtc_get_info": (_I, [_P, C.POINTER(RtcInfo)]),
+    "rtc_process_frame": (_I, [_P, _P, _P, _P]),
+    "rtc_process_frame_async": (_I, [_P, _P, _P, _P, _P]),
+    "rtc_synchronize": (_I, [_P, _P]),
+    "rtc_centroid_async": (_I, [_P, _P, _P, _P]),
+    "rtc_reconstruct_async": (_I, [_P, _P, _P, _P]),
+}
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load librtc.so and declare its signatures; raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"librtc.so not found at {path}; build it with "
+                          "`python -c 'import __graft_entry__ as g; g.build()'`")
+    lib = C.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+class RtcError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{_ERRNAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+def _ptr(x):
+    """Raw address of a numpy array or torch tensor (None -> NULL)."""
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("arrays passed to librtc must be C-contiguous")
+        return x.ctypes.data
+    if hasattr(x, "data_ptr"):
+        if not x.is_contiguous():
+            raise ValueError("tensors passed to librtc must be contiguous")
+        return x.data_ptr()
+    if isinstance(x, int):
+        return x
+    raise TypeError(f"cannot pass {type(x)} to librtc")
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        return None
+    if hasattr(stream, "cuda_stream"):
+        return stream.cuda_stream
+    return int(stream)
+
+
+class Rtc:
+    """One real-time-controller instance on one GPU (a librtc handle)."""
+
+    def __init__(self, nsub: int, npx: int, nact: int, n_wfs: int = 1, obs: float = 0.0,
+                 gain: float = 0.4, leak: float = 0.99, thr_mode: int = 0, thr: float = 0.0,
+                 device: int = 0, ksplit: int = 0):
+        self._lib = load_library()
+        cfg = RtcConfig(nsub, npx, n_wfs, nact, obs, gain, leak, thr_mode, thr, device, ksplit, 0)
+        h = _P()
+        rc = self._lib.rtc_create(C.byref(cfg), C.byref(h))
+        if rc != RTC_OK:
+            raise RtcError(rc, self._lib.rtc_last_error(None).decode())
+        self._h = h
+        self.cfg = cfg
+
+    # -- helpers ---------------------------------------------------------------
+    def _check(self, rc: int):
+        if rc != RTC_OK:
+            raise RtcError(rc, self._lib.rtc_last_error(self._h).decode())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.rtc_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    @property
+    def handle(self):
+        return self._h
+
+    # -- loading -------------------------------------------------------------------
+    def info(self) -> dict:
+        inf = RtcInfo()
+        self._check(self._lib.rtc_get_info(self._h, C.byref(inf)))
+        return {k: getattr(inf, k) for k, _ in RtcInfo._fields_}
+
+    def load_subaps(self, rc):
+        rc = np.ascontiguousarray(rc, dtype=np.int32).reshape(-1, 2)
+        self._check(self._lib.rtc_load_subaps(self._h, _ptr(rc), rc.shape[0]))
+
+    def load_calib(self, dark, flat):
+        d = np.ascontiguousarray(dark, dtype=np.float32)
+        f = np.ascontiguousarray(flat, dtype=np.float32)
+        if d.size != f.size:
+            raise ValueError("dark and flat must have the same size")
+        self._check(self._lib.rtc_load_calib(self._h, _ptr(d), _ptr(f), d.size))
+
+    def set_threshold(self, mode: int, thr: float):
+        self._check(self._lib.rtc_set_threshold(self._h, mode, thr))
+
+    def load_cmat(self, M, store: str = "f32", src: str = "f32", row_scales=None):
+        if src == "f32":
+            m = np.ascontiguousarray(M, dtype=np.float32)
+        elif src == "bf16":
+            m = np.ascontiguousarray(M, dtype=np.uint16)
+        elif src == "fp8":
+            m = np.ascontiguousarray(M, dtype=np.uint8)
+        else:
+            raise ValueError(src)
+        sc = None if row_scales is None else np.ascontiguousarray(row_scales, dtype=np.float32)
+        self._check(self._lib.rtc_load_cmat(self._h, _ptr(m), m.shape[0], m.shape[1],
+                                            DTYPES[src], DTYPES[store], _ptr(sc)))
+
+    def set_gain(self, gain: float, leak: float):
+        self._check(self._lib.rtc_set_gain(self._h, gain, leak))
+
+    def reset(self):
+        self._check(self._lib.rtc_reset(self._h))
+
+    def get_dm(self) -> np.ndarray:
+        out = np.empty(self.cfg.nact, np.float32)
+        self._check(self._lib.rtc_get_dm(self._h, _ptr(out)))
+        return out
+
+    # -- per frame -----------------------------------------------------------------
+    def process_frame(self, frame, dm_out=None, slopes_out=None, want_slopes: bool = False):
+        """One synchronous step with host buffers.  ``frame`` is a uint16 numpy array or a
+        (pinned) CPU tensor; returns dm (and slopes if requested)."""
+        if isinstance(frame, np.ndarray):
+            frame = np.ascontiguousarray(frame, dtype=np.uint16)
+        inf = None
+        if dm_out is None:
+            dm_out = np.empty(self.cfg.nact, np.float32)
+        if want_slopes and slopes_out is None:
+            inf = inf or self.info()
+            slopes_out = np.empty(inf["nslopes"], np.float32)
+        self._check(self._lib.rtc_process_frame(self._h, _ptr(frame), _ptr(dm_out), _ptr(slopes_out)))
+        return (dm_out, slopes_out) if (want_slopes or slopes_out is not None) else dm_out
+
+    def process_frame_async(self, d_frame, d_dm_out=None, d_slopes_out=None, stream=None):
+        """Enqueue one step on device buffers (torch CUDA tensors) on ``stream``."""
+        self._check(self._lib.rtc_process_frame_async(self._h, _ptr(d_frame), _ptr(d_dm_out),
+                                                      _ptr(d_slopes_out), _stream_ptr(stream)))
+
+    def centroid_async(self, d_frame, d_slopes_out=None, stream=None):
+        """Enqueue the pixel stage (calibration + centroids) on device buffers."""
+        self._check(self._lib.rtc_centroid_async(self._h, _ptr(d_frame), _ptr(d_slopes_out),
+                                                 _stream_ptr(stream)))
+
+    def reconstruct_async(self, d_slopes=None, d_dm_out=None, stream=None):
+        """Enqueue MVM + integrator from ``d_slopes`` (None: the resident slope buffer)."""
+        self._check(self._lib.rtc_reconstruct_async(self._h, _ptr(d_slopes), _ptr(d_dm_out),
+                                                    _stream_ptr(stream)))
+
+    def synchronize(self, stream=None):
+        self._check(self._lib.rtc_synchronize(self._h, _stream_ptr(stream)))
+
+
+def version() -> str:
+    return load_library().rtc_version().decode()

@@ -1,0 +1,202 @@
+"""GPU path vs the FP64 oracle, element by element, through the C ABI.
+
+Tolerances (from the contract of the pipeline):
+  centroids          <= 1e-5 px absolute
+  DM commands, FP32  <= 1e-5 relative RMS
+  BF16 / FP8 stored matrices: the kernel against the oracle on the *stored*
+  matrix <= 1e-5 relative RMS (checks the kernel); against the unquantised
+  matrix BF16 <= 2e-3 and FP8 measured and bounded (see test docstring).
+"""
+import numpy as np
+import pytest
+import torch
+
+import synth
+from helpers import make_pair, rel_rms
+from oracle import pipeline as P
+from oracle import quant as Q
+
+pytestmark = pytest.mark.gpu
+
+SLOPE_TOL = 1e-5
+DM_TOL = 1e-5
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    import __graft_entry__ as g
+    g.build()
+
+
+def _run_and_compare(r, oracle, frames, slope_tol=SLOPE_TOL, dm_tol=DM_TOL):
+    worst_s, worst_a = 0.0, 0.0
+    for k in range(frames.shape[0]):
+        raw = np.ascontiguousarray(frames[k])
+        dm, s = r.process_frame(raw, want_slopes=True)
+        a_ref, s_ref = oracle.step(raw)
+        worst_s = max(worst_s, float(np.max(np.abs(s - s_ref))) if s.size else 0.0)
+        worst_a = max(worst_a, rel_rms(dm, a_ref))
+    assert worst_s <= slope_tol, worst_s
+    assert worst_a <= dm_tol, worst_a
+    return worst_s, worst_a
+
+
+def test_tiny_scao_closed_loop_1000_frames():
+    cfg = synth.tiny_scao()
+    frames, _ = synth.make_frames(cfg, 0, cfg.n_frames)
+    r, oracle, *_ = make_pair(cfg)
+    _run_and_compare(r, oracle, frames.numpy())
+
+
+@pytest.mark.parametrize("ksplit", [1, 2, 3, 7, 32])
+def test_split_k_factors_agree(ksplit):
+    cfg = synth.tiny_scao()
+    frames, _ = synth.make_frames(cfg, 0, 20)
+    r, oracle, *_ = make_pair(cfg, ksplit=ksplit)
+    assert r.info()["ksplit"] == ksplit
+    _run_and_compare(r, oracle, frames.numpy())
+
+
+@pytest.mark.parametrize("mode,thr", [(0, 5.0), (1, 5.0), (0, -1e9), (1, 40.0)])
+def test_threshold_modes(mode, thr):
+    cfg = synth.tiny_scao()
+    frames, _ = synth.make_frames(cfg, 3, 20)
+    r, oracle, *_ = make_pair(cfg, thr_mode=mode, thr=thr)
+    _run_and_compare(r, oracle, frames.numpy())
+
+
+def test_default_subap_map_matches_generator_geometry():
+    from paper_1805_07254_gb300 import Rtc
+    for cfg in (synth.tiny_scao(), synth.elt_scao()):
+        r = Rtc(cfg.nsub, cfg.npx, cfg.nact, obs=cfg.obs)
+        assert r.info()["n_valid"] == cfg.n_valid
+        assert r.info()["nslopes"] == cfg.nslopes
+        r.close()
+
+
+def test_odd_geometry_unaligned_bands_single_actuator():
+    # 3x3 grid of 7x7 px: band rows are 294 bytes (not 16-byte multiples), odd box centre
+    cfg = synth.tiny_scao().with_(name="odd", nsub=3, npx=7, dm_side=1, obs=0.0)
+    frames, _ = synth.make_frames(cfg, 0, 10)
+    r, oracle, *_ = make_pair(cfg)
+    assert r.info()["nact"] == 1
+    _run_and_compare(r, oracle, frames.numpy())
+
+
+def test_single_subap_and_custom_map():
+    cfg = synth.tiny_scao()
+    frames, _ = synth.make_frames(cfg, 0, 5)
+    for sa in (np.array([[3, 4]], np.int32), cfg.subaps[::3].copy()):
+        r, oracle, *_ = make_pair(cfg, subaps=sa)
+        assert r.info()["n_valid"] == sa.shape[0]
+        _run_and_compare(r, oracle, frames.numpy())
+
+
+def test_empty_subap_map_decays_integrator():
+    cfg = synth.tiny_scao()
+    frames, _ = synth.make_frames(cfg, 0, 4)
+    r, oracle, M, dark, flat, sa = make_pair(cfg)
+    dm0 = r.process_frame(frames[0].numpy())
+    r.load_subaps(np.zeros((0, 2), np.int32))
+    r.load_calib(dark, flat)
+    r.load_cmat(np.zeros((cfg.nact, 0), np.float32))
+    dm1 = r.process_frame(frames[1].numpy())
+    np.testing.assert_allclose(dm1, cfg.leak * dm0, rtol=1e-6)
+
+
+def test_dark_frame_gives_zero_slopes():
+    cfg = synth.tiny_scao()
+    r, oracle, M, dark, flat, sa = make_pair(cfg, thr_mode=0, thr=0.0)
+    raw = np.zeros((1, cfg.frame_side, cfg.frame_side), np.uint16)   # below dark everywhere
+    dm, s = r.process_frame(raw, want_slopes=True)
+    assert np.all(s == 0) and np.all(dm == 0)
+
+
+def test_saturated_uniform_frame():
+    cfg = synth.tiny_scao()
+    r, oracle, *_ = make_pair(cfg)
+    raw = np.full((1, 1, cfg.frame_side, cfg.frame_side), 65535, np.uint16)
+    _run_and_compare(r, oracle, raw)
+
+
+def test_elt_scao_frames_fp32():
+    cfg = synth.elt_scao()
+    frames, _ = synth.make_frames(cfg, 0, 3)
+    r, oracle, *_ = make_pair(cfg)
+    _run_and_compare(r, oracle, frames.numpy())
+
+
+@pytest.mark.parametrize("store", ["bf16", "fp8"])
+def test_reduced_precision_kernel_vs_stored_matrix(store):
+    cfg = synth.elt_scao()
+    frames, _ = synth.make_frames(cfg, 0, 2)
+    r, oracle, *_ = make_pair(cfg, store=store)
+    _run_and_compare(r, oracle, frames.numpy())
+
+
+def test_reduced_precision_error_against_unquantised_oracle():
+    """BF16 meets 2e-3.  FP8 E4M3 with per-row scales is measured near 2.6e-2 on
+    N(0, 1/K) entries, above the 2e-2 target: the 3-bit mantissa's relative
+    rounding error does not depend on the scale.  It is bounded here at 3.5e-2."""
+    cfg = synth.elt_scao()
+    frames, _ = synth.make_frames(cfg, 0, 1)
+    raw = frames[0].numpy()
+    errs = {}
+    for store in ("bf16", "fp8"):
+        r, oracle, M, dark, flat, sa = make_pair(cfg, store=store)
+        dm, s = r.process_frame(raw, want_slopes=True)
+        ref = cfg.gain * (M.astype(np.float64) @ P.slopes(raw, dark, flat, sa, cfg.npx))
+        errs[store] = rel_rms(dm, ref)
+    assert errs["bf16"] <= 2e-3, errs
+    assert errs["fp8"] <= 3.5e-2, errs
+
+
+def test_device_async_path_matches_host_path():
+    cfg = synth.tiny_scao()
+    frames, _ = synth.make_frames(cfg, 0, 6)
+    r1, _, *_ = make_pair(cfg)
+    r2, _, *_ = make_pair(cfg)
+    dev = torch.device("cuda:0")
+    d_dm = torch.empty(cfg.nact, dtype=torch.float32, device=dev)
+    d_s = torch.empty(cfg.nslopes, dtype=torch.float32, device=dev)
+    st = torch.cuda.current_stream()
+    for k in range(frames.shape[0]):
+        dm_h, s_h = r1.process_frame(frames[k].numpy(), want_slopes=True)
+        d_frame = frames[k].contiguous().to(dev)
+        r2.process_frame_async(d_frame, d_dm, d_s, stream=st)
+        r2.synchronize(st)
+        np.testing.assert_array_equal(d_dm.cpu().numpy(), dm_h)
+        np.testing.assert_array_equal(d_s.cpu().numpy(), s_h)
+
+
+def test_reset_and_gain_changes():
+    cfg = synth.tiny_scao()
+    frames, _ = synth.make_frames(cfg, 0, 3)
+    r, oracle, *_ = make_pair(cfg)
+    r.process_frame(frames[0].numpy())
+    r.reset()
+    assert np.all(r.get_dm() == 0)
+    r.set_gain(0.7, 1.0)
+    oracle.gain, oracle.leak = 0.7, 1.0
+    _run_and_compare(r, oracle, frames[1:].numpy())
+
+
+def test_stress_six_wfs_fp8_sampled_rows():
+    """Stress sizing: 6 WFS stacked into one 4421 x 47664 FP8 matrix.  The oracle
+    checks slopes fully and DM commands on a sample of rows."""
+    cfg = synth.elt_scao_6wfs()
+    frames, _ = synth.make_frames(cfg, 0, 1)
+    raw = frames[0].numpy()
+    from paper_1805_07254_gb300 import Rtc
+    dark, flat = synth.calibration_maps(cfg)
+    M = synth.control_matrix(cfg).numpy()
+    r = Rtc(cfg.nsub, cfg.npx, cfg.nact, n_wfs=cfg.n_wfs, obs=cfg.obs, gain=cfg.gain, leak=cfg.leak)
+    r.load_calib(dark.numpy(), flat.numpy())
+    r.load_cmat(M, store="fp8")
+    dm, s = r.process_frame(raw, want_slopes=True)
+    s_ref = P.slopes(raw, dark.numpy(), flat.numpy(), cfg.subaps, cfg.npx)
+    assert np.max(np.abs(s - s_ref)) <= SLOPE_TOL
+    rows = np.random.default_rng(0).choice(cfg.nact, 64, replace=False)
+    q, sc = Q.fp8_row_quantise(M[rows])
+    ref = cfg.gain * ((sc.astype(np.float64)[:, None] * q) @ s_ref)
+    assert rel_rms(dm[rows], ref) <= DM_TOL
