@@ -231,7 +231,7 @@ def time_steps(torch, r, d_frames, d_dm, flush, st, n_steps, n_warm):
     flush_out = torch.empty((), dtype=flush.dtype, device=flush.device)
 
     def one(i, ev):
-        torch.sum(flush, out=flush_out)
+        torch.sum(flush, dim=0, out=flush_out)
         if ev:
             ev[0].record(st)
         r.centroid_async(d_frames[i % nF], stream=st)
@@ -317,7 +317,7 @@ def ours(args):
     e2e_us = []
     flush_out = torch.empty((), dtype=torch.float32, device=dev)
     for i in range(args.warmup + n_e2e):
-        torch.sum(flush, out=flush_out)
+        torch.sum(flush, dim=0, out=flush_out)
         torch.cuda.synchronize()
         t0 = time.perf_counter_ns()
         r.process_frame(pin_frames[i % n_frames], dm_out=pin_dm)
