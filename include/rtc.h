@@ -89,8 +89,9 @@ typedef struct rtc_handle rtc_handle;
 /* Build/version string of the library (static storage; never NULL). */
 const char* rtc_version(void);
 
-/* Message of the last failure on h (or of the last failed rtc_create when h is
- * NULL).  Static or handle-owned storage valid until the next call on h. */
+/* Message of the last failure on h (or, when h is NULL, of the last failed call
+ * without a handle: rtc_create, rtc_mvm_integrate_noalloc).  Static or
+ * handle-owned storage valid until the next call on h. */
 const char* rtc_last_error(const rtc_handle* h);
 
 /* Validate cfg and allocate the handle's resident device state.  The default
@@ -175,6 +176,45 @@ int rtc_reconstruct_async(rtc_handle* h, const float* d_slopes, float* d_dm_out,
 /* Block until all work enqueued by the handle on `stream` (NULL: own stream) is
  * done, and report any device error.  Errors: RTC_EDEVICE. */
 int rtc_synchronize(rtc_handle* h, void* stream);
+
+/* Largest sizes rtc_mvm_integrate_noalloc accepts (its scratch is fixed at load). */
+#define RTC_NOALLOC_MAX_NACT   8192
+#define RTC_NOALLOC_MAX_KSPLIT 16
+
+/* Reconstruction + leaky integrator (the work of rtc_reconstruct_async) for
+ * callers that must not allocate device memory.  The paper has no counterpart:
+ * this entry point exists for hosts such as a hard-real-time control thread,
+ * which cannot afford the implicit device synchronisation and unbounded latency
+ * of cudaMalloc inside its loop, or a plugin inside a larger RTC framework that
+ * receives every device buffer from the framework and may not allocate its own.
+ * It needs no handle and allocates nothing: the split-K scratch lives in a
+ * static device array of about 520 KiB, held by every GPU that loads the library
+ * until the process exits.
+ *
+ * Buffers (all device memory on the current device, owned by the caller):
+ *   d_M          [nact][kpad] matrix in the stored type `store` (rtc_dtype),
+ *                rows zero-padded, 16-byte aligned; kpad a multiple of 16;
+ *   d_row_scales [nact] FP32 row scales (FP8 only, else may be NULL);
+ *   d_s          [kpad] FP32 slopes, zero-padded, 16-byte aligned;
+ *   d_a          [nact] FP32 integrator state, updated in place:
+ *                a <- leak * a + gain * (M s);
+ *   d_dm_out     [nact] FP32 copy of the new state, or NULL.
+ * nact must be in 1..RTC_NOALLOC_MAX_NACT and ksplit in 1..RTC_NOALLOC_MAX_KSPLIT;
+ * larger sizes are rejected with RTC_EINVAL (message in rtc_last_error(NULL)).
+ * The work is enqueued on `stream` (a cudaStream_t; NULL is the legacy default
+ * stream) without synchronising.
+ *
+ * The first call on a device looks up the scratch array's device address (this
+ * may load the library's device code); make that first call before any stream
+ * capture.  Every call on a device shares the one scratch array, which keeps the
+ * last call's contents; each call clears the counters it needs before its kernel.
+ * Calls whose work overlaps on the GPU (unordered streams) race on the scratch
+ * and give wrong results: order them on one stream.
+ * Errors: RTC_EINVAL, RTC_EDEVICE. */
+int rtc_mvm_integrate_noalloc(const void* d_M, int32_t store, const float* d_row_scales,
+                              int32_t nact, int32_t kpad, const float* d_s, float* d_a,
+                              float* d_dm_out, float gain, float leak, int32_t ksplit,
+                              void* stream);
 
 #ifdef __cplusplus
 }

@@ -269,6 +269,33 @@ cudaError_t launch_mvm_integrate(const rtc_handle* h, const float* d_s, float* d
     }
 }
 
+cudaError_t launch_mvm_raw(int store, const void* d_M, const float* d_scale, int nact, int kpad,
+                           const float* d_s, int ksplit, float* d_partial, unsigned* d_count,
+                           float* d_a, float* d_dm_out, float gain, float leak, cudaStream_t st) {
+    dim3 grid((nact + kMvmRows - 1) / kMvmRows, ksplit);
+    const uint4* M = static_cast<const uint4*>(d_M);
+    switch (store) {
+        case RTC_F32:
+            mvm_splitk_kernel<RTC_F32, 2><<<grid, kMvmThreads, 0, st>>>(
+                M, kpad / Epc<RTC_F32>::v, nact, d_s, d_scale, ksplit, d_partial, d_count, d_a,
+                d_dm_out, gain, leak);
+            break;
+        case RTC_BF16:
+            mvm_splitk_kernel<RTC_BF16, 2><<<grid, kMvmThreads, 0, st>>>(
+                M, kpad / Epc<RTC_BF16>::v, nact, d_s, d_scale, ksplit, d_partial, d_count, d_a,
+                d_dm_out, gain, leak);
+            break;
+        case RTC_FP8_E4M3:
+            mvm_splitk_kernel<RTC_FP8_E4M3, 2><<<grid, kMvmThreads, 0, st>>>(
+                M, kpad / Epc<RTC_FP8_E4M3>::v, nact, d_s, d_scale, ksplit, d_partial, d_count,
+                d_a, d_dm_out, gain, leak);
+            break;
+        default:
+            return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
 cudaError_t launch_quantise(int store, const float* d_src, int nact, int K, int kpad, void* d_dst,
                             float* d_scale, cudaStream_t st) {
     if (nact <= 0) return cudaSuccess;

@@ -154,6 +154,8 @@ int enqueue_step(rtc_handle* h, const uint16_t* d_frame, float* d_dm_out, float*
 
 }  // namespace
 
+void rtc_set_global_error(const char* msg) { g_create_error = msg; }
+
 extern "C" {
 
 const char* rtc_version(void) { return "librtc 0.1 (sm_103a)"; }

@@ -60,9 +60,19 @@ cudaError_t launch_calib_cog(const rtc_handle* h, const uint16_t* d_frame, float
 cudaError_t launch_mvm_integrate(const rtc_handle* h, const float* d_s, float* d_dm_out,
                                  cudaStream_t st);
 
+// The same split-K MVM + integrator on caller-described buffers: matrix [nact][kpad]
+// in the stored type, s [kpad], partial scratch [ksplit][nact], counters
+// [ceil(nact/kMvmRows)] that must be zero on entry.
+cudaError_t launch_mvm_raw(int store, const void* d_M, const float* d_scale, int nact, int kpad,
+                           const float* d_s, int ksplit, float* d_partial, unsigned* d_count,
+                           float* d_a, float* d_dm_out, float gain, float leak, cudaStream_t st);
+
 // Convert an FP32 device matrix [nact][K] into the stored layout [nact][kpad].
 cudaError_t launch_quantise(int store, const float* d_src, int nact, int K, int kpad,
                             void* d_dst, float* d_scale, cudaStream_t st);
+
+// Message returned by rtc_last_error(NULL) for failures of calls without a handle.
+void rtc_set_global_error(const char* msg);
 
 // Smallest dynamic shared memory the pixel stage needs for this geometry.
 size_t calib_cog_smem_bytes(const rtc_handle* h);

@@ -55,6 +55,8 @@ SIGNATURES = {
     "rtc_synchronize": (_I, [_P, _P]),
     "rtc_centroid_async": (_I, [_P, _P, _P, _P]),
     "rtc_reconstruct_async": (_I, [_P, _P, _P, _P]),
+    "rtc_mvm_integrate_noalloc": (_I, [_P, C.c_int32, _P, C.c_int32, C.c_int32, _P, _P, _P,
+                                       C.c_float, C.c_float, C.c_int32, _P]),
 }
 
 _lib = None
@@ -225,6 +227,19 @@ class Rtc:
 
     def synchronize(self, stream=None):
         self._check(self._lib.rtc_synchronize(self._h, _stream_ptr(stream)))
+
+
+def mvm_integrate_noalloc(d_M, store: str, d_row_scales, nact: int, kpad: int, d_s, d_a,
+                          d_dm_out=None, gain: float = 0.4, leak: float = 0.99, ksplit: int = 1,
+                          stream=None):
+    """Reconstruction + integrator on caller-owned device buffers, with no device
+    allocation by the library (see rtc_mvm_integrate_noalloc in include/rtc.h)."""
+    lib = load_library()
+    rc = lib.rtc_mvm_integrate_noalloc(_ptr(d_M), DTYPES[store], _ptr(d_row_scales), nact, kpad,
+                                       _ptr(d_s), _ptr(d_a), _ptr(d_dm_out), gain, leak, ksplit,
+                                       _stream_ptr(stream))
+    if rc != RTC_OK:
+        raise RtcError(rc, lib.rtc_last_error(None).decode())
 
 
 def version() -> str:
