@@ -1,24 +1,29 @@
 // Pixel calibration, centre-of-gravity centroiding and slope packing
 // (Sec. 2.1, Fig. 3 (a) and (b)).
 //
-// One block per (subaperture row, WFS).  The block stages the row's band of
-// npx detector rows (npx * side uint16 pixels, contiguous in the frame) into
-// shared memory with 16-byte loads, then each warp takes one valid
-// subaperture of the band at a time: it calibrates the npx*npx pixels
+// One warp per valid subaperture (of one WFS).  The stage is latency-bound (a
+// 740x740 frame plus its calibration data is ~4 MB), so every lane issues all of
+// its loads -- raw pixels from the frame, dark and gain values from the
+// subap-major calibration arrays -- before any arithmetic, and the whole frame
+// costs about one HBM round trip.  Each lane then calibrates its pixels
 //     p = (raw - dark) * gain,   gain = 1/flat,
-// applies the threshold, and forms the flux and the two first moments about
-// the box centre c = (npx-1)/2 with compensated (TwoSum) FP32 accumulation,
-// reduced across the warp by a fixed xor butterfly.  Lane 0 writes
+// applies the threshold (the comparison on the FP32 value), and accumulates the
+// flux and the two first moments about the box centre c = (npx-1)/2 with
+// compensated (TwoSum) FP32 sums, reduced across the warp by a fixed xor
+// butterfly.  Lane 0 writes
 //     s[i] = Sx/F,  s[n_valid + i] = Sy/F   (0 when F <= 0),
-// the x-then-y order of the Fig. 3 caption.
+// the x-then-y order of the Fig. 3 caption (per WFS block).
 //
-// Dark and gain values are kept per valid subaperture, contiguous
-// (subap-major [n_valid][npx*npx]), so their loads are coalesced and only
-// valid pixels are read.
+// Dark and gain are kept per valid subaperture, contiguous (subap-major
+// [n_valid][npx*npx]), so their loads are coalesced and only valid pixels are
+// read.
 
 #include "rtc_internal.h"
 
 namespace {
+
+constexpr int kWarpsPerBlock = kCalibThreads / 32;
+constexpr int kPixPerLane = 8;          // loads in flight per lane per pass (npx <= 16 in one pass)
 
 struct CompSum {
     float s, c;
@@ -43,100 +48,90 @@ __device__ __forceinline__ void comp_warp_reduce(CompSum& a) {
     }
 }
 
-// Copy n uint16 values from global src to shared memory, 16 bytes at a time
-// where the source is aligned.  Returns the shared-memory address at which
-// element 0 landed (shifted so that the aligned part stays aligned).
-__device__ __forceinline__ const uint16_t* stage_band(const uint16_t* __restrict__ src, int n,
-                                                      unsigned char* smem) {
-    const uintptr_t a = reinterpret_cast<uintptr_t>(src);
-    const int shift = static_cast<int>(a & 15);          // bytes past the previous 16-B line
-    uint16_t* dst = reinterpret_cast<uint16_t*>(smem + shift);
-    int head = ((16 - shift) & 15) >> 1;                 // elements until src is 16-B aligned
-    if (head > n) head = n;
-    const int nvec = (n - head) >> 3;
-    for (int q = threadIdx.x; q < head; q += blockDim.x) dst[q] = src[q];
-    const uint4* vs = reinterpret_cast<const uint4*>(src + head);
-    uint4* vd = reinterpret_cast<uint4*>(dst + head);
-    for (int q = threadIdx.x; q < nvec; q += blockDim.x) vd[q] = __ldg(vs + q);
-    for (int q = head + 8 * nvec + threadIdx.x; q < n; q += blockDim.x) dst[q] = src[q];
-    return dst;
-}
-
+// NPX > 0: box size known at compile time (divisions by constants, exact unrolling);
+// NPX == 0: any box size, given at run time.
+template <int NPX>
 __global__ void __launch_bounds__(kCalibThreads)
-calib_cog_kernel(const uint16_t* __restrict__ frame, int side, int npx, int n_valid,
-                 const int32_t* __restrict__ bands, const int32_t* __restrict__ subcol,
-                 const float* __restrict__ dark, const float* __restrict__ gainmap,
-                 int thr_mode, float thr, float* __restrict__ s_out) {
-    extern __shared__ __align__(16) unsigned char smem[];
-    const int b = blockIdx.x;
-    const int w = blockIdx.y;
-    const int row = bands[3 * b + 0];
-    const int first = bands[3 * b + 1];
-    const int count = bands[3 * b + 2];
-    const size_t plane = static_cast<size_t>(side) * side;
-    const uint16_t* src = frame + w * plane + static_cast<size_t>(row) * npx * side;
-    const uint16_t* px = stage_band(src, npx * side, smem);
-    __syncthreads();
-
+calib_cog_kernel(const uint16_t* __restrict__ frame, int side, int npx_rt, int n_valid, int n_wfs,
+                 const int2* __restrict__ rc, const float* __restrict__ dark,
+                 const float* __restrict__ gainmap, int thr_mode, float thr,
+                 float* __restrict__ s_out) {
+    constexpr int kJ = NPX > 0 ? (NPX * NPX + 31) / 32 : kPixPerLane;
+    const int npx = NPX > 0 ? NPX : npx_rt;
     const int lane = threadIdx.x & 31;
-    const int warp = threadIdx.x >> 5;
-    const int nwarps = blockDim.x >> 5;
+    const int gw = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+    if (gw >= n_valid * n_wfs) return;
+    const int w = gw / n_valid;
+    const int i = gw - w * n_valid;
+    const int2 pos = rc[i];                                  // (row, col) on the grid
     const int npp = npx * npx;
     const float cc = 0.5f * static_cast<float>(npx - 1);
-    float* s_w = s_out + static_cast<size_t>(w) * 2 * n_valid;
+    const uint16_t* box = frame + static_cast<size_t>(w) * side * side +
+                          static_cast<size_t>(pos.x) * npx * side + static_cast<size_t>(pos.y) * npx;
+    const size_t base = (static_cast<size_t>(w) * n_valid + i) * npp;
+    const float* dk = dark + base;
+    const float* gk = gainmap + base;
 
-    for (int k = warp; k < count; k += nwarps) {
-        const int i = first + k;
-        const int col0 = subcol[i] * npx;
-        const size_t base = (static_cast<size_t>(w) * n_valid + i) * npp;
-        const float* dk = dark + base;
-        const float* gk = gainmap + base;
-        CompSum F{0.f, 0.f}, Sx{0.f, 0.f}, Sy{0.f, 0.f};
-        for (int q = lane; q < npp; q += 32) {
-            const int y = q / npx;
-            const int x = q - y * npx;
-            const float raw = static_cast<float>(px[y * side + col0 + x]);
-            float p = __fmul_rn(__fsub_rn(raw, __ldg(dk + q)), __ldg(gk + q));
-            if (thr_mode == 0) {
-                p = (p < thr) ? 0.f : p;
-            } else {
-                p = (p > thr) ? __fsub_rn(p, thr) : 0.f;
+    CompSum F{0.f, 0.f}, Sx{0.f, 0.f}, Sy{0.f, 0.f};
+    for (int q0 = 0; q0 < npp; q0 += 32 * kJ) {
+        float raw[kJ], dv[kJ], gv[kJ];
+        int xs[kJ], ys[kJ];
+#pragma unroll
+        for (int j = 0; j < kJ; ++j) {
+            const int q = q0 + lane + 32 * j;
+            ys[j] = q / npx;
+            xs[j] = q - ys[j] * npx;
+            if (q < npp) {
+                raw[j] = static_cast<float>(__ldg(box + ys[j] * side + xs[j]));
+                dv[j] = __ldg(dk + q);
+                gv[j] = __ldg(gk + q);
             }
-            comp_add(F, p);
-            comp_add(Sx, __fmul_rn(p, static_cast<float>(x) - cc));
-            comp_add(Sy, __fmul_rn(p, static_cast<float>(y) - cc));
         }
-        comp_warp_reduce(F);
-        comp_warp_reduce(Sx);
-        comp_warp_reduce(Sy);
-        if (lane == 0) {
-            const float f = F.s + F.c;
-            const float sx = Sx.s + Sx.c;
-            const float sy = Sy.s + Sy.c;
-            const bool ok = f > 0.f;
-            s_w[i] = ok ? sx / f : 0.f;
-            s_w[n_valid + i] = ok ? sy / f : 0.f;
+#pragma unroll
+        for (int j = 0; j < kJ; ++j) {
+            if (q0 + lane + 32 * j < npp) {
+                float p = __fmul_rn(__fsub_rn(raw[j], dv[j]), gv[j]);
+                if (thr_mode == 0) {
+                    p = (p < thr) ? 0.f : p;
+                } else {
+                    p = (p > thr) ? __fsub_rn(p, thr) : 0.f;
+                }
+                comp_add(F, p);
+                comp_add(Sx, __fmul_rn(p, static_cast<float>(xs[j]) - cc));
+                comp_add(Sy, __fmul_rn(p, static_cast<float>(ys[j]) - cc));
+            }
         }
+    }
+    comp_warp_reduce(F);
+    comp_warp_reduce(Sx);
+    comp_warp_reduce(Sy);
+    if (lane == 0) {
+        const float f = F.s + F.c;
+        const float sx = Sx.s + Sx.c;
+        const float sy = Sy.s + Sy.c;
+        const bool ok = f > 0.f;
+        float* s_w = s_out + static_cast<size_t>(w) * 2 * n_valid;
+        s_w[i] = ok ? sx / f : 0.f;
+        s_w[n_valid + i] = ok ? sy / f : 0.f;
     }
 }
 
 }  // namespace
 
-size_t calib_cog_smem_bytes(const rtc_handle* h) {
-    return static_cast<size_t>(h->cfg.npx) * h->side * sizeof(uint16_t) + 16;
-}
-
-cudaError_t calib_cog_configure(size_t smem_bytes) {
-    return cudaFuncSetAttribute(calib_cog_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                static_cast<int>(smem_bytes));
-}
-
 cudaError_t launch_calib_cog(const rtc_handle* h, const uint16_t* d_frame, float* d_s,
                              cudaStream_t st) {
-    if (h->nbands == 0) return cudaSuccess;
-    dim3 grid(h->nbands, h->cfg.n_wfs);
-    calib_cog_kernel<<<grid, kCalibThreads, calib_cog_smem_bytes(h), st>>>(
-        d_frame, h->side, h->cfg.npx, h->n_valid, h->d_band, h->d_subcol, h->d_dark,
-        h->d_gainmap, h->thr_mode, h->thr, d_s);
+    const int warps = h->n_valid * h->cfg.n_wfs;
+    if (warps == 0) return cudaSuccess;
+    const int blocks = (warps + kWarpsPerBlock - 1) / kWarpsPerBlock;
+#define RTC_CALIB_ARGS                                                                           \
+    d_frame, h->side, h->cfg.npx, h->n_valid, h->cfg.n_wfs, h->d_rc, h->d_dark, h->d_gainmap, \
+        h->thr_mode, h->thr, d_s
+    switch (h->cfg.npx) {
+        case 8: calib_cog_kernel<8><<<blocks, kCalibThreads, 0, st>>>(RTC_CALIB_ARGS); break;
+        case 10: calib_cog_kernel<10><<<blocks, kCalibThreads, 0, st>>>(RTC_CALIB_ARGS); break;
+        case 16: calib_cog_kernel<16><<<blocks, kCalibThreads, 0, st>>>(RTC_CALIB_ARGS); break;
+        default: calib_cog_kernel<0><<<blocks, kCalibThreads, 0, st>>>(RTC_CALIB_ARGS); break;
+    }
+#undef RTC_CALIB_ARGS
     return cudaGetLastError();
 }

@@ -209,17 +209,6 @@ mvm_splitk_kernel(const uint4* __restrict__ M, int chunks_per_row, int nact,
     }
 }
 
-template <int DT>
-cudaError_t launch_typed(const rtc_handle* h, const float* d_s, float* d_dm_out, cudaStream_t st) {
-    const int nact = h->cfg.nact;
-    const int cpr = h->kpad / Epc<DT>::v;
-    dim3 grid((nact + kMvmRows - 1) / kMvmRows, h->ksplit);
-    mvm_splitk_kernel<DT, 2><<<grid, kMvmThreads, 0, st>>>(
-        static_cast<const uint4*>(h->d_M), cpr, nact, d_s, h->d_scale, h->ksplit, h->d_partial,
-        h->d_count, h->d_a, d_dm_out, h->gain, h->leak);
-    return cudaGetLastError();
-}
-
 // --- load-time quantisers -----------------------------------------------------
 
 __global__ void pad_bf16_kernel(const float* __restrict__ src, int K, int kpad,
@@ -258,16 +247,6 @@ __global__ void quant_fp8_kernel(const float* __restrict__ src, int K, int kpad,
 }
 
 }  // namespace
-
-cudaError_t launch_mvm_integrate(const rtc_handle* h, const float* d_s, float* d_dm_out,
-                                 cudaStream_t st) {
-    switch (h->store) {
-        case RTC_F32: return launch_typed<RTC_F32>(h, d_s, d_dm_out, st);
-        case RTC_BF16: return launch_typed<RTC_BF16>(h, d_s, d_dm_out, st);
-        case RTC_FP8_E4M3: return launch_typed<RTC_FP8_E4M3>(h, d_s, d_dm_out, st);
-        default: return cudaErrorInvalidValue;
-    }
-}
 
 cudaError_t launch_mvm_raw(int store, const void* d_M, const float* d_scale, int nact, int kpad,
                            const float* d_s, int ksplit, float* d_partial, unsigned* d_count,

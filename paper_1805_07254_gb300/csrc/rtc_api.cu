@@ -100,18 +100,7 @@ int apply_subaps(rtc_handle* h, const std::vector<int32_t>& rc) {
                 return fail(h, RTC_EINVAL, "subap map must be strictly increasing in row-major order (entry %d)", i);
         }
     }
-    std::vector<int32_t> bands, cols(nv);
-    for (int i = 0; i < nv; ++i) {
-        cols[i] = rc[2 * i + 1];
-        if (i == 0 || rc[2 * i] != rc[2 * i - 2]) {
-            bands.push_back(rc[2 * i]);
-            bands.push_back(i);
-            bands.push_back(0);
-        }
-        bands.back() += 1;
-    }
-    free_dev(h->d_band);
-    free_dev(h->d_subcol);
+    free_dev(h->d_rc);
     free_dev(h->d_dark);
     free_dev(h->d_gainmap);
     free_dev(h->d_M);
@@ -121,17 +110,27 @@ int apply_subaps(rtc_handle* h, const std::vector<int32_t>& rc) {
     h->n_valid = nv;
     h->nslopes = 2 * nv * h->cfg.n_wfs;
     h->kpad = (h->nslopes + 15) / 16 * 16;
-    h->nbands = static_cast<int>(bands.size() / 3);
     h->store = -1;
     h->calib_loaded = false;
     if (nv > 0) {
-        RTC_CUDA(h, cudaMalloc(&h->d_band, bands.size() * sizeof(int32_t)));
-        RTC_CUDA(h, cudaMemcpy(h->d_band, bands.data(), bands.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
-        RTC_CUDA(h, cudaMalloc(&h->d_subcol, nv * sizeof(int32_t)));
-        RTC_CUDA(h, cudaMemcpy(h->d_subcol, cols.data(), nv * sizeof(int32_t), cudaMemcpyHostToDevice));
+        RTC_CUDA(h, cudaMalloc(&h->d_rc, nv * sizeof(int2)));
+        RTC_CUDA(h, cudaMemcpy(h->d_rc, rc.data(), nv * sizeof(int2), cudaMemcpyHostToDevice));
     }
     RTC_CUDA(h, cudaMalloc(&h->d_s, std::max(h->kpad, 16) * sizeof(float)));
     RTC_CUDA(h, cudaMemset(h->d_s, 0, std::max(h->kpad, 16) * sizeof(float)));
+    return RTC_OK;
+}
+
+// Read (and clear) the device status word after the stream has drained.
+int take_status(rtc_handle* h, cudaStream_t st) {
+    RTC_CUDA(h, cudaMemcpyAsync(h->h_status, h->d_status, sizeof(int), cudaMemcpyDeviceToHost, st));
+    RTC_CUDA(h, cudaStreamSynchronize(st));
+    const int code = *h->h_status;
+    if (code != 0) {
+        RTC_CUDA(h, cudaMemsetAsync(h->d_status, 0, sizeof(int), st));
+        RTC_CUDA(h, cudaStreamSynchronize(st));
+        return fail(h, code, "a bounded device wait expired (results of this step are invalid)");
+    }
     return RTC_OK;
 }
 
@@ -192,13 +191,10 @@ int rtc_create(const rtc_config* cfg, rtc_handle** out) {
     h->ksplit = choose_ksplit(h);
     DeviceScope ds(c.device);
     int rcode = RTC_OK;
-    const size_t smem = static_cast<size_t>(c.npx) * h->side * sizeof(uint16_t) + 16;
-    int smem_optin = 0;
-    cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c.device);
-    if (smem > static_cast<size_t>(smem_optin)) {
-        rcode = fail(nullptr, RTC_EINVAL, "a band of npx*side pixels (%zu B) exceeds shared memory", smem);
-    } else if (calib_cog_configure(static_cast<size_t>(smem_optin)) != cudaSuccess) {
-        rcode = fail(nullptr, RTC_EDEVICE, "cannot configure the pixel-stage shared memory");
+    cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, c.device);
+    if (h->num_sms < 1) h->num_sms = 1;
+    if (mvm_stream_configure() != cudaSuccess) {
+        rcode = fail(nullptr, RTC_EDEVICE, "cannot configure the reconstruction kernel");
     } else if (cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking) != cudaSuccess) {
         rcode = fail(nullptr, RTC_EDEVICE, "cudaStreamCreate failed");
     } else {
@@ -207,10 +203,13 @@ int rtc_create(const rtc_config* cfg, rtc_handle** out) {
         if (cudaMalloc(&h->d_a, c.nact * sizeof(float)) != cudaSuccess ||
             cudaMalloc(&h->d_partial, static_cast<size_t>(kMaxKsplit) * c.nact * sizeof(float)) != cudaSuccess ||
             cudaMalloc(&h->d_count, nrb * sizeof(unsigned)) != cudaSuccess ||
-            cudaMalloc(&h->d_frame, frame_elems * sizeof(uint16_t)) != cudaSuccess) {
+            cudaMalloc(&h->d_frame, frame_elems * sizeof(uint16_t)) != cudaSuccess ||
+            cudaMalloc(&h->d_status, sizeof(int)) != cudaSuccess ||
+            cudaMallocHost(&h->h_status, sizeof(int)) != cudaSuccess) {
             rcode = fail(nullptr, RTC_ENOMEM, "device allocation failed");
         } else if (cudaMemset(h->d_a, 0, c.nact * sizeof(float)) != cudaSuccess ||
-                   cudaMemset(h->d_count, 0, nrb * sizeof(unsigned)) != cudaSuccess) {
+                   cudaMemset(h->d_count, 0, nrb * sizeof(unsigned)) != cudaSuccess ||
+                   cudaMemset(h->d_status, 0, sizeof(int)) != cudaSuccess) {
             rcode = fail(nullptr, RTC_EDEVICE, "cudaMemset failed");
         } else {
             rcode = apply_subaps(h, default_subaps(c.nsub, c.obs));
@@ -229,8 +228,7 @@ int rtc_destroy(rtc_handle* h) {
     if (!h) return RTC_OK;
     DeviceScope ds(h->cfg.device);
     if (h->stream) cudaStreamSynchronize(h->stream);
-    free_dev(h->d_band);
-    free_dev(h->d_subcol);
+    free_dev(h->d_rc);
     free_dev(h->d_dark);
     free_dev(h->d_gainmap);
     free_dev(h->d_M);
@@ -240,6 +238,9 @@ int rtc_destroy(rtc_handle* h) {
     free_dev(h->d_partial);
     free_dev(h->d_count);
     free_dev(h->d_frame);
+    free_dev(h->d_status);
+    if (h->h_status) cudaFreeHost(h->h_status);
+    h->h_status = nullptr;
     if (h->stream) cudaStreamDestroy(h->stream);
     delete h;
     return RTC_OK;
@@ -400,8 +401,7 @@ int rtc_process_frame(rtc_handle* h, const uint16_t* frame, float* dm_out, float
     RTC_CUDA(h, cudaMemcpyAsync(dm_out, h->d_a, h->cfg.nact * sizeof(float), cudaMemcpyDeviceToHost, h->stream));
     if (slopes_out)
         RTC_CUDA(h, cudaMemcpyAsync(slopes_out, h->d_s, h->nslopes * sizeof(float), cudaMemcpyDeviceToHost, h->stream));
-    RTC_CUDA(h, cudaStreamSynchronize(h->stream));
-    return RTC_OK;
+    return take_status(h, h->stream);
 }
 
 int rtc_process_frame_async(rtc_handle* h, const uint16_t* d_frame, float* d_dm_out,
@@ -447,7 +447,7 @@ int rtc_synchronize(rtc_handle* h, void* stream) {
     cudaStream_t st = stream ? static_cast<cudaStream_t>(stream) : h->stream;
     RTC_CUDA(h, cudaStreamSynchronize(st));
     RTC_CUDA(h, cudaGetLastError());
-    return RTC_OK;
+    return take_status(h, st);
 }
 
 }  // extern "C"

@@ -25,19 +25,18 @@ struct rtc_handle {
     int kpad = 0;               // padded matrix row length (elements)
     int store = -1;             // rtc_dtype of the resident matrix, -1 when none
     int ksplit = 1;
-    int nbands = 0;             // subaperture rows holding at least one valid subap
     float gain = 0.f, leak = 1.f;
     int thr_mode = 0;
     float thr = 0.f;
     bool calib_loaded = false;
 
     cudaStream_t stream = nullptr;
+    int num_sms = 1;                // streaming multiprocessors of the device
 
     std::vector<int32_t> rc;    // host copy of the subaperture map (row, col) pairs
 
     // device buffers (owned)
-    int32_t* d_band = nullptr;      // [nbands][3]: grid row, first valid index, count
-    int32_t* d_subcol = nullptr;    // [n_valid] grid column of each valid subap
+    int2* d_rc = nullptr;           // [n_valid] (row, col) grid position of each valid subap
     float* d_dark = nullptr;        // [n_wfs][n_valid][npx*npx] dark, subap-major
     float* d_gainmap = nullptr;     // [n_wfs][n_valid][npx*npx] 1/flat, subap-major
     void* d_M = nullptr;            // [nact][kpad] in the stored type
@@ -47,6 +46,8 @@ struct rtc_handle {
     float* d_partial = nullptr;     // [kMaxKsplit][nact] split-K partial products (scratch)
     unsigned* d_count = nullptr;    // [ceil(nact/kMvmRows)] arrival counters (scratch, self-resetting)
     uint16_t* d_frame = nullptr;    // [n_wfs][side][side] staging for host frames
+    int* d_status = nullptr;        // device-side error word (RTC_ETIMEDOUT from bounded waits)
+    int* h_status = nullptr;        // pinned host mirror of d_status
 
     std::string err;
 };
@@ -56,7 +57,10 @@ struct rtc_handle {
 cudaError_t launch_calib_cog(const rtc_handle* h, const uint16_t* d_frame, float* d_s,
                              cudaStream_t st);
 
-// Split-K MVM with the fused fixed-order partial tree and leaky integrator.
+// Streaming MVM (persistent, TMA bulk copies) with the fixed-order partial tree and
+// the leaky integrator; d_partial holds shared-row-group partials, d_count their
+// self-resetting arrival counters.
+cudaError_t mvm_stream_configure();
 cudaError_t launch_mvm_integrate(const rtc_handle* h, const float* d_s, float* d_dm_out,
                                  cudaStream_t st);
 
@@ -73,7 +77,3 @@ cudaError_t launch_quantise(int store, const float* d_src, int nact, int K, int 
 
 // Message returned by rtc_last_error(NULL) for failures of calls without a handle.
 void rtc_set_global_error(const char* msg);
-
-// Smallest dynamic shared memory the pixel stage needs for this geometry.
-size_t calib_cog_smem_bytes(const rtc_handle* h);
-cudaError_t calib_cog_configure(size_t smem_bytes);
