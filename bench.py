@@ -86,22 +86,28 @@ def measured_peaks():
         return FALLBACK_HBM_GBS, "fallback"
 
 
-def mvm_source_digest():
+KERNEL_SOURCES = ("frame_kernel.cu", "stream_mvm.cuh", "pixel.cuh")
+
+
+def kernel_source_digest():
+    """sha256[:16] over the sources of the fused frame kernel."""
     h = hashlib.sha256()
-    with open(os.path.join(ROOT, "paper_1805_07254_gb300", "csrc", "mvm.cu"), "rb") as f:
-        h.update(f.read())
+    for name in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_1805_07254_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
     return h.hexdigest()[:16]
 
 
 def recorded_traffic(workload):
-    """DRAM bytes per MVM launch from an ncu capture of the current kernel source, else None."""
+    """DRAM bytes per frame-kernel launch from an ncu capture of the current kernel
+    sources, else None."""
     p = os.path.join(ROOT, "profiles", "dram_traffic.txt")
     if not os.path.exists(p):
         return None
-    dig = mvm_source_digest()
+    dig = kernel_source_digest()
     for line in open(p):
         parts = line.split()
-        if len(parts) == 4 and not line.startswith("#") and parts[0] == "mvm" \
+        if len(parts) == 4 and not line.startswith("#") and parts[0] == "frame" \
                 and parts[1] == workload and parts[2] == dig:
             return float(parts[3])
     return None
@@ -224,38 +230,48 @@ def workload_config(cfg, store, info=None):
 
 
 # --------------------------------------------------------------------------- our arm
-def time_steps(torch, r, d_frames, d_dm, flush, st, n_steps, n_warm):
-    """Per-step (pixel stage us, MVM us, step us) from CUDA events on stream st."""
+def time_steps(torch, r, d_frames, d_dm, flush, st, n_steps, n_warm, fused=True):
+    """Per-step device times (us) from CUDA events on stream st.
+
+    fused: one rtc_process_frame_async call per step (the fused frame kernel);
+    returns (step,).  Otherwise the two stage calls with an event between them;
+    returns (pixel stage, reconstruction, step)."""
     E = torch.cuda.Event
     nF = len(d_frames)
     flush_out = torch.empty((), dtype=flush.dtype, device=flush.device)
+    nev = 2 if fused else 3
 
     def one(i, ev):
         torch.sum(flush, dim=0, out=flush_out)
         if ev:
             ev[0].record(st)
-        r.centroid_async(d_frames[i % nF], stream=st)
+        if fused:
+            r.process_frame_async(d_frames[i % nF], d_dm, stream=st)
+        else:
+            r.centroid_async(d_frames[i % nF], stream=st)
+            if ev:
+                ev[1].record(st)
+            r.reconstruct_async(None, d_dm, stream=st)
         if ev:
-            ev[1].record(st)
-        r.reconstruct_async(None, d_dm, stream=st)
-        if ev:
-            ev[2].record(st)
+            ev[-1].record(st)
 
     with torch.cuda.stream(st):
         for i in range(n_warm):
             one(i, None)
         st.synchronize()
-        evs = [(E(enable_timing=True), E(enable_timing=True), E(enable_timing=True))
-               for _ in range(n_steps)]
+        evs = [tuple(E(enable_timing=True) for _ in range(nev)) for _ in range(n_steps)]
         for b0 in range(0, n_steps, BATCH):
             nb = min(BATCH, n_steps - b0)
             torch.cuda._sleep(int(2e6))          # device head start while the host enqueues
             for i in range(b0, b0 + nb):
                 one(i, evs[i])
         st.synchronize()
+    r.synchronize(st)                            # raises if a bounded device wait expired
+    step = [evs[i][0].elapsed_time(evs[i][-1]) * 1e3 for i in range(n_steps)]
+    if fused:
+        return (step,)
     cog = [evs[i][0].elapsed_time(evs[i][1]) * 1e3 for i in range(n_steps)]
     mvm = [evs[i][1].elapsed_time(evs[i][2]) * 1e3 for i in range(n_steps)]
-    step = [evs[i][0].elapsed_time(evs[i][2]) * 1e3 for i in range(n_steps)]
     return cog, mvm, step
 
 
@@ -298,16 +314,21 @@ def ours(args):
     sampler = ClockSampler(local)
     sampler.start()
     t_wall = time.perf_counter()
-    cog, mvm, step = time_steps(torch, r, d_frames, d_dm, flush, st, args.steps, args.warmup)
+    (step,) = time_steps(torch, r, d_frames, d_dm, flush, st, args.steps, args.warmup, fused=True)
     t_wall = time.perf_counter() - t_wall
     clocks = sampler.stop()
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
 
-    s_step, s_mvm, s_cog = stats_us(step), stats_us(mvm), stats_us(cog)
+    # the same frames through the two stage kernels, for the per-stage split
+    n_stage = min(args.steps, 2000)
+    cog, mvm, step2 = time_steps(torch, r, d_frames, d_dm, flush, st, n_stage, args.warmup, fused=False)
+
+    s_step, s_mvm, s_cog, s_step2 = stats_us(step), stats_us(mvm), stats_us(cog), stats_us(step2)
     mvm_bytes = info["matrix_bytes"] + 4 * info["nslopes"] + 8 * cfg.nact
     step_bytes = mvm_bytes + info["frame_bytes"] + info["calib_bytes"]
+    frame_gbs = step_bytes / (s_step["mean"] * 1e-6) / 1e9
     mvm_gbs = mvm_bytes / (s_mvm["mean"] * 1e-6) / 1e9
 
     # e2e: the synchronous host-buffer C call, pinned frame in, DM commands out
@@ -333,15 +354,20 @@ def ours(args):
                 continue
             rv = controller(store)
             iv = rv.info()
-            c2, m2, s2 = time_steps(torch, rv, d_frames, d_dm, flush, st, min(args.steps, 2000),
-                                    args.warmup)
+            (s2,) = time_steps(torch, rv, d_frames, d_dm, flush, st, min(args.steps, 2000),
+                               args.warmup, fused=True)
+            _, m2, _ = time_steps(torch, rv, d_frames, d_dm, flush, st, min(args.steps, 1000),
+                                  args.warmup, fused=False)
             sv, mv = stats_us(s2), stats_us(m2)
             mb = iv["matrix_bytes"] + 4 * iv["nslopes"] + 8 * cfg.nact
+            fb = mb + iv["frame_bytes"] + iv["calib_bytes"]
             variants[store] = {"p50_us": round(sv["p50"], 3), "p99_us": round(sv["p99"], 3),
+                               "p999_us": round(sv["p999"], 3),
                                "rms_jitter_us": round(sv["rms_jitter"], 3),
-                               "mvm_us_mean": round(mv["mean"], 3),
-                               "mvm_hbm_gbs": round(mb / (mv["mean"] * 1e-6) / 1e9, 1),
-                               "mvm_frac_of_peak": round(mb / (mv["mean"] * 1e-6) / 1e9 / hbm_peak, 4)}
+                               "frame_hbm_gbs": round(fb / (sv["mean"] * 1e-6) / 1e9, 1),
+                               "frame_frac_of_peak": round(fb / (sv["mean"] * 1e-6) / 1e9 / hbm_peak, 4),
+                               "stage_mvm_us_mean": round(mv["mean"], 3),
+                               "stage_mvm_hbm_gbs": round(mb / (mv["mean"] * 1e-6) / 1e9, 1)}
             rv.close()
 
     # max over ranks (worst replica)
@@ -369,18 +395,19 @@ def ours(args):
         "p999_us": round(s_step["p999"], 3), "rms_jitter_us": round(s_step["rms_jitter"], 3),
         "peak_to_peak_us": round(s_step["peak_to_peak"], 3), "mean_us": round(s_step["mean"], 3),
         "frames_per_s": round(world * 1e6 / s_step["mean"], 1),
-        "stage_us_p50": {"calib_cog": round(s_cog["p50"], 3), "mvm_integrate": round(s_mvm["p50"], 3)},
-        "mvm_hbm_gbs": round(mvm_gbs, 1),
-        "step_hbm_frac": round(step_bytes / (s_step["mean"] * 1e-6) / 1e9 / hbm_peak, 4),
-        "roofline": {"kernel": "mvm_splitk_kernel", "bound": "hbm", "achieved": round(mvm_gbs, 1),
+        "stage_path_us_p50": {"calib_cog_kernel": round(s_cog["p50"], 3),
+                              "mvm_stream_kernel": round(s_mvm["p50"], 3),
+                              "step_two_kernels": round(s_step2["p50"], 3)},
+        "stage_mvm_hbm_gbs": round(mvm_gbs, 1),
+        "roofline": {"kernel": "frame_kernel", "bound": "hbm", "achieved": round(frame_gbs, 1),
                      "peak": hbm_peak, "peak_kind": peak_kind, "unit": "GB/s",
-                     "frac": round(mvm_gbs / hbm_peak, 4), "traffic": traffic,
-                     "algorithmic_bytes": mvm_bytes},
+                     "frac": round(frame_gbs / hbm_peak, 4), "traffic": traffic,
+                     "algorithmic_bytes": step_bytes},
         "e2e": {"value": round(s_e2e["p50"], 3), "unit": "us", "p99_us": round(s_e2e["p99"], 3),
                 "rms_jitter_us": round(s_e2e["rms_jitter"], 3),
                 "h2d_bytes_per_step": info["frame_bytes"], "d2h_bytes_per_step": 4 * cfg.nact,
                 "steps": n_e2e},
-        "gpu_launches": 2 * args.steps,
+        "gpu_launches": args.steps,
         "clocks": clocks,
         "timed_wall_s_incl_flush": round(t_wall, 3),
         "variants": variants,

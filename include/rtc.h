@@ -177,6 +177,61 @@ int rtc_reconstruct_async(rtc_handle* h, const float* d_slopes, float* d_dm_out,
  * done, and report any device error.  Errors: RTC_EDEVICE. */
 int rtc_synchronize(rtc_handle* h, void* stream);
 
+/* ---- persistent real-time loop ---------------------------------------------
+ * The paper's RTC runs its threads continuously and hands work over through
+ * spinning on flags rather than sleeping (Sec. 2.3.2); latency is measured from
+ * the last pixel to the DM demand being ready, jitter is its variation (Sec. 3).
+ * rtc_run_loop is the GPU form: one persistent kernel keeps calibration, matrix
+ * and integrator resident and loops over frames.  A host thread publishes each
+ * frame in a ring of pinned, device-mapped buffers by setting a sequence flag;
+ * the kernel's blocks spin (bounded) on that flag, read the pixels directly from
+ * host memory, compute the DM commands, write them to mapped host memory and
+ * publish a completion record with device timestamps. */
+
+#define RTC_LOOP_SLOTS 8            /* frame slots in the host ring */
+
+/* Fill dst (pinned host memory, uint16 [n_wfs][H][W]) with frame k.  Return 0,
+ * or non-zero to end the loop early.  Called on a library-owned thread. */
+typedef int (*rtc_frame_source)(void* user, uint64_t k, uint16_t* dst);
+
+/* Receives the DM commands (float32 [nact], valid during the call) of frame k,
+ * on the thread that called rtc_run_loop, after the frame's latency is taken. */
+typedef void (*rtc_dm_sink)(void* user, uint64_t k, const float* dm);
+
+typedef struct rtc_loop_config {
+    uint64_t n_frames;           /* frames to process (> 0) */
+    double rate_hz;              /* publish at this rate; 0: each frame as soon as the
+                                    previous one's DM commands are out */
+    rtc_frame_source source;     /* fills each frame, or NULL to cycle `preload` */
+    void* source_user;
+    const uint16_t* preload;     /* host frames [n_preload][n_wfs][H][W] (source == NULL) */
+    int32_t n_preload;           /* 1 .. RTC_LOOP_SLOTS */
+    rtc_dm_sink sink;            /* or NULL */
+    void* sink_user;
+    int64_t* e2e_ns;             /* [n_frames] publish -> DM visible on the host, or NULL */
+    int64_t* dev_ns;             /* [n_frames] frame seen -> DM written, device clock, or NULL */
+} rtc_loop_config;
+
+/* Latency statistics of one rtc_run_loop call.  "e2e": host clock, from the flag
+ * that publishes the frame to the moment the host sees the completion record
+ * (the DM commands are in host memory).  "dev": device clock, from the first
+ * block seeing the frame to the last block finishing its DM commands. */
+typedef struct rtc_stats {
+    uint64_t frames;             /* frames completed */
+    double frames_per_s;         /* completed frames / (last completion - first publish) */
+    double e2e_p50_us, e2e_p99_us, e2e_p999_us, e2e_mean_us, e2e_rms_jitter_us, e2e_p2p_us;
+    double dev_p50_us, dev_p99_us, dev_p999_us, dev_mean_us, dev_rms_jitter_us, dev_p2p_us;
+} rtc_stats;
+
+/* Run the persistent loop for cfg->n_frames frames and return when they are done
+ * (or the source stopped).  The handle must have calibration and matrix loaded;
+ * the integrator state carries over from and to the per-frame calls.  One loop at
+ * a time per handle.  Every device wait is bounded: a frame that is not published
+ * within 2 s, or a grid barrier that does not complete within 200 ms, ends the
+ * loop with RTC_ETIMEDOUT.  Errors: RTC_EINVAL, RTC_ESTATE, RTC_ENOMEM,
+ * RTC_EDEVICE, RTC_ETIMEDOUT. */
+int rtc_run_loop(rtc_handle* h, const rtc_loop_config* cfg, rtc_stats* stats);
+
 /* Largest sizes rtc_mvm_integrate_noalloc accepts (its scratch is fixed at load). */
 #define RTC_NOALLOC_MAX_NACT   8192
 #define RTC_NOALLOC_MAX_KSPLIT 16

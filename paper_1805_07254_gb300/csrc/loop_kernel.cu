@@ -1,0 +1,211 @@
+// Persistent real-time loop kernel: the per-frame pipeline of Sec. 2.1 / Fig. 3,
+// frame after frame, in one cooperative launch.
+//
+// The paper's RTC keeps its worker threads running and synchronises them by
+// spinning on flags instead of sleeping (Sec. 2.3.2).  Here every block keeps
+// running across frames:
+//   1. thread 0 of each block spins (bounded, 2 s) on the frame's sequence flag
+//      in pinned host memory (a system-scope acquire load); a stop value ends
+//      the loop;
+//   2. the consumer warps compute the block's share of the slopes, reading the
+//      pixels straight from the host ring with loads that bypass the caches (the
+//      slot is rewritten between its uses);
+//   3. a bounded grid barrier makes the slope vector (double-buffered by frame
+//      parity) visible to all blocks;
+//   4. the streaming reconstruction + integrator; DM commands go to the device
+//      state and to the frame's slot in mapped host memory;
+//   5. the last block to finish publishes the completion record (sequence,
+//      device time the frame was seen, device time the commands were written).
+// The producer warps stream the matrix frame after frame; their barrier phases
+// continue across frames, so the next frame's first tiles are already in flight
+// while a frame is being finished.
+
+#include "pixel.cuh"
+#include "stream_mvm.cuh"
+
+namespace {
+
+using namespace rtc_mvm;
+
+constexpr unsigned long long kFrameWaitNs = 2000ull * 1000 * 1000;   // 2 s for a frame to arrive
+constexpr unsigned long long kStop = ~0ull;
+
+struct LoopArgs {
+    rtc_pixel::PixelArgs px;           // frame and s are set per frame
+    Args mv;                           // s and dm_out are set per frame
+    const uint16_t* frames;            // mapped host ring [nslot][frame_elems]
+    unsigned long long frame_elems;
+    const unsigned long long* seq;     // mapped host [nslot]: frame k published as k + 1
+    float* dm_ring;                    // mapped host [nslot][nact]
+    rtc_loop_done* done;               // mapped host [nslot]
+    float* s_buf;                      // device [2][kpad]
+    unsigned long long* gridbar;       // device, zero at launch
+    unsigned long long* donectr;       // device, zero at launch
+    unsigned long long* t_seen;        // device [2]
+    unsigned long long n_frames;
+    int nslot;
+    int kpad;
+};
+
+__device__ __forceinline__ unsigned long long ld_acquire_sys(const unsigned long long* p) {
+    unsigned long long v;
+    asm volatile("ld.acquire.sys.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release_sys(unsigned long long* p, unsigned long long v) {
+    asm volatile("st.release.sys.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+template <int DT, bool S_SMEM, int NPX>
+__global__ void __launch_bounds__(kThreads, 1) loop_kernel(LoopArgs L) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ Shared sh;
+    __shared__ int stop_now;
+    const int tid = threadIdx.x;
+    const unsigned long long G = gridDim.x;
+    if (tid == 0) init_shared(sh);
+    __syncthreads();
+    const Plan pl = make_plan<DT, S_SMEM>(L.mv, smem);
+
+    if (tid >= kConsumers) {
+        // producers: the matrix does not depend on the frame
+        if ((tid & 31) < kTeams) {
+            const int team = tid & 31;
+            int tl = 0;
+            for (unsigned long long k = 0; k < L.n_frames && !sh.abort_flag; ++k)
+                tl = produce(L.mv, pl, sh, team, tl, k + 1 == L.n_frames);
+        }
+        return;
+    }
+
+    const int nt = L.px.n_valid * L.px.n_wfs;
+    const int i0 = static_cast<int>(static_cast<long long>(nt) * blockIdx.x / gridDim.x);
+    const int i1 = static_cast<int>(static_cast<long long>(nt) * (blockIdx.x + 1) / gridDim.x);
+    const int slot_lane = 2 * (tid >> 5) + ((tid >> 4) & 1);
+    int tile = 0;
+    for (unsigned long long k = 0; k < L.n_frames; ++k) {
+        const int slot = static_cast<int>(k % L.nslot);
+        // 1. wait for frame k
+        if (tid == 0) {
+            int stop = 0;
+            const unsigned long long t0 = global_ns();
+            while (true) {
+                const unsigned long long v = ld_acquire_sys(L.seq + slot);
+                if (v == kStop) {
+                    stop = 1;
+                    break;
+                }
+                if (v >= k + 1) break;
+                if (global_ns() - t0 > kFrameWaitNs) {
+                    atomicExch(L.mv.status, RTC_ETIMEDOUT);
+                    stop = 1;
+                    break;
+                }
+            }
+            if (blockIdx.x == 0 && !stop) L.t_seen[k & 1] = global_ns();
+            if (stop) sh.abort_flag = 1;            // the producers stop too
+            stop_now = stop;
+        }
+        consumer_sync();
+        if (stop_now) break;
+
+        // 2. this block's share of the slopes, pixels read from the host ring
+        const uint16_t* frame = L.frames + static_cast<size_t>(slot) * L.frame_elems;
+        float* s_k = L.s_buf + static_cast<size_t>(k & 1) * L.kpad;
+        for (int base = i0; base < i1; base += 2 * kConsumerWarps) {
+            const int gi = base + slot_lane;
+            rtc_pixel::subap_slopes<NPX, rtc_pixel::kPixelVolatile, 16>(L.px, frame, s_k, gi, gi < i1,
+                                                                        tid & 31);
+        }
+
+        // 3. the whole slope vector visible to every block
+        consumer_sync();
+        if (tid == 0) grid_barrier(L.gridbar, G * (k + 1), L.mv.status, &sh.abort_flag);
+        consumer_sync();
+        if (sh.abort_flag) break;
+
+        // 4. reconstruction and integrator
+        consumer_prologue<DT, S_SMEM, true>(L.mv, pl, tid, s_k);
+        tile = consume<DT, S_SMEM, true>(L.mv, pl, sh, tid, tile, s_k,
+                                         L.dm_ring + static_cast<size_t>(slot) * L.mv.nact);
+
+        // 5. the last block to finish publishes the completion record
+        consumer_sync();
+        if (tid == 0) {
+            __threadfence_system();
+            const unsigned long long prev = atomicAdd(L.donectr, 1ull);
+            if (prev + 1 == G * (k + 1)) {
+                rtc_loop_done* d = L.done + slot;
+                d->t_seen = __ldcg(L.t_seen + (k & 1));
+                d->t_done = global_ns();
+                __threadfence_system();
+                st_release_sys(&d->seq, k + 1);
+            }
+        }
+    }
+}
+
+template <int DT, bool S, int NPX>
+cudaError_t launch_t(const Launch& Lc, LoopArgs a, cudaStream_t st) {
+    void* args[] = {&a};
+    return cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(loop_kernel<DT, S, NPX>),
+                                       dim3(Lc.G), dim3(kThreads), args, Lc.smem, st);
+}
+
+template <int DT>
+cudaError_t launch_dt(rtc_handle* h, const LoopLaunch& ll, cudaStream_t st) {
+    const Launch Lc = plan_launch(h, Epc<DT>::v);
+    if (!Lc.ok) return cudaErrorInvalidValue;
+    LoopArgs a;
+    a.px = pixel_args(h, nullptr, nullptr);
+    a.mv = make_args(h, nullptr, nullptr, Lc.nst, Epc<DT>::v);
+    a.frames = ll.d_frames;
+    a.frame_elems = ll.frame_elems;
+    a.seq = ll.d_seq;
+    a.dm_ring = ll.d_dm;
+    a.done = ll.d_done;
+    a.s_buf = h->d_sbuf;
+    a.gridbar = h->d_gridbar;
+    a.donectr = h->d_donectr;
+    a.t_seen = h->d_tseen;
+    a.n_frames = ll.n_frames;
+    a.nslot = ll.nslot;
+    a.kpad = h->kpad;
+    const bool npx10 = h->cfg.npx == 10;
+    if (Lc.s_in_smem)
+        return npx10 ? launch_t<DT, true, 10>(Lc, a, st) : launch_t<DT, true, 0>(Lc, a, st);
+    return npx10 ? launch_t<DT, false, 10>(Lc, a, st) : launch_t<DT, false, 0>(Lc, a, st);
+}
+
+template <int DT, bool S, int NPX>
+cudaError_t configure_t() {
+    return cudaFuncSetAttribute(loop_kernel<DT, S, NPX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                static_cast<int>(kDynSmemBudget));
+}
+
+template <int DT>
+cudaError_t configure_dt() {
+    cudaError_t e = configure_t<DT, true, 10>();
+    if (e == cudaSuccess) e = configure_t<DT, true, 0>();
+    if (e == cudaSuccess) e = configure_t<DT, false, 10>();
+    if (e == cudaSuccess) e = configure_t<DT, false, 0>();
+    return e;
+}
+
+}  // namespace
+
+cudaError_t loop_kernel_configure() {
+    cudaError_t e = configure_dt<RTC_F32>();
+    if (e == cudaSuccess) e = configure_dt<RTC_BF16>();
+    if (e == cudaSuccess) e = configure_dt<RTC_FP8_E4M3>();
+    return e;
+}
+
+cudaError_t launch_loop(rtc_handle* h, const LoopLaunch& ll, cudaStream_t st) {
+    switch (h->store) {
+        case RTC_F32: return launch_dt<RTC_F32>(h, ll, st);
+        case RTC_BF16: return launch_dt<RTC_BF16>(h, ll, st);
+        case RTC_FP8_E4M3: return launch_dt<RTC_FP8_E4M3>(h, ll, st);
+        default: return cudaErrorInvalidValue;
+    }
+}

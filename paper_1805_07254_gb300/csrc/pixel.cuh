@@ -1,0 +1,143 @@
+// Device code of the pixel stage (Sec. 2.1, Fig. 3 (a)-(b)), shared by the
+// stand-alone centroid kernel and the fused frame kernel.
+//
+// One warp takes one valid subaperture of one WFS.  The stage is latency-bound
+// (a 740x740 frame plus its calibration data is ~4 MB), so every lane issues all
+// of its loads -- raw pixels from the frame, dark and gain values from the
+// subap-major calibration arrays -- before any arithmetic.  Each lane then
+// calibrates its pixels
+//     p = (raw - dark) * gain,   gain = 1/flat,
+// applies the threshold (the comparison on the FP32 value), and accumulates the
+// flux and the two first moments about the box centre c = (npx-1)/2 with
+// compensated (TwoSum) FP32 sums, reduced across the warp by a fixed xor
+// butterfly.  Lane 0 writes
+//     s[i] = Sx/F,  s[n_valid + i] = Sy/F   (0 when F <= 0),
+// the x-then-y order of the Fig. 3 caption (per WFS block).
+#pragma once
+
+#include "rtc_internal.h"
+
+namespace rtc_pixel {
+
+constexpr int kPixPerLane = 8;   // loads in flight per lane per pass for a run-time box size
+
+struct CompSum {
+    float s, c;
+};
+
+// TwoSum accumulation: the rounding error of every addition is kept in c.
+__device__ __forceinline__ void comp_add(CompSum& a, float v) {
+    float t = __fadd_rn(a.s, v);
+    float bp = __fsub_rn(t, a.s);
+    float e = __fadd_rn(__fsub_rn(a.s, __fsub_rn(t, bp)), __fsub_rn(v, bp));
+    a.s = t;
+    a.c = __fadd_rn(a.c, e);
+}
+
+// Reduce over aligned groups of L lanes (L = 16 or 32) with a fixed xor butterfly.
+template <int L>
+__device__ __forceinline__ void comp_group_reduce(CompSum& a) {
+#pragma unroll
+    for (int off = L / 2; off > 0; off >>= 1) {
+        float os = __shfl_xor_sync(0xffffffffu, a.s, off);
+        float oc = __shfl_xor_sync(0xffffffffu, a.c, off);
+        a.c = __fadd_rn(a.c, oc);
+        comp_add(a, os);
+    }
+}
+
+struct PixelArgs {
+    const uint16_t* frame;   // [n_wfs][side][side]
+    int side, npx, n_valid, n_wfs;
+    const int2* rc;          // [n_valid] (row, col)
+    const float* dark;       // [n_wfs][n_valid][npx*npx]
+    const float* gainmap;    // [n_wfs][n_valid][npx*npx]
+    int thr_mode;
+    float thr;
+    float* s;                // [n_wfs][2][n_valid]
+};
+
+// How raw pixels are read: through the read-only path (a frame that does not change
+// while the kernel runs), or fetched fresh every time (a frame buffer that a host
+// producer rewrites while a persistent kernel keeps running).
+enum PixelLoad { kPixelReadOnly = 0, kPixelVolatile = 1 };
+
+template <int LD>
+__device__ __forceinline__ uint16_t load_pixel(const uint16_t* ptr) {
+    if (LD == kPixelVolatile) return __ldcv(ptr);
+    return __ldg(ptr);
+}
+
+// Slopes of subaperture gi (= w * n_valid + i) by an aligned group of L lanes
+// (L = 32: the whole warp; L = 16: each half-warp takes its own subaperture).
+// Every lane of the warp must call it (the reductions shuffle across the warp);
+// a group with valid == false computes nothing and writes nothing.
+// NPX > 0: box size known at compile time; NPX == 0: p.npx at run time.
+// frame and s_out: this frame's pixels and slope vector (PixelArgs' own fields are
+// not used, so that a persistent kernel can switch buffers per frame cheaply).
+template <int NPX, int LD, int L>
+__device__ __forceinline__ void subap_slopes(const PixelArgs& p, const uint16_t* __restrict__ frame,
+                                             float* __restrict__ s_out, int gi, bool valid, int lane) {
+    constexpr int kJ = NPX > 0 ? (NPX * NPX + L - 1) / L : kPixPerLane;
+    const int npx = NPX > 0 ? NPX : p.npx;
+    const int l = lane & (L - 1);
+    const int w = valid ? gi / p.n_valid : 0;
+    const int i = valid ? gi - w * p.n_valid : 0;
+    const int npp = valid ? npx * npx : 0;
+    const int2 pos = valid ? p.rc[i] : make_int2(0, 0);
+    const float cc = 0.5f * static_cast<float>(npx - 1);
+    const uint16_t* box = frame + static_cast<size_t>(w) * p.side * p.side +
+                          static_cast<size_t>(pos.x) * npx * p.side + static_cast<size_t>(pos.y) * npx;
+    const size_t base = (static_cast<size_t>(w) * p.n_valid + i) * npp;
+    const float* dk = p.dark + base;
+    const float* gk = p.gainmap + base;
+
+    CompSum F{0.f, 0.f}, Sx{0.f, 0.f}, Sy{0.f, 0.f};
+    for (int q0 = 0; q0 < npp; q0 += L * kJ) {
+        float raw[kJ], dv[kJ], gv[kJ];
+#pragma unroll
+        for (int j = 0; j < kJ; ++j) {
+            const int q = q0 + l + L * j;
+            if (q < npp) {
+                const int y = q / npx;
+                raw[j] = static_cast<float>(load_pixel<LD>(box + y * p.side + (q - y * npx)));
+                dv[j] = __ldg(dk + q);
+                gv[j] = __ldg(gk + q);
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < kJ; ++j) {
+            const int q = q0 + l + L * j;
+            if (q < npp) {
+                const int y = q / npx;
+                const int x = q - y * npx;
+                float v = __fmul_rn(__fsub_rn(raw[j], dv[j]), gv[j]);
+                if (p.thr_mode == 0) {
+                    v = (v < p.thr) ? 0.f : v;
+                } else {
+                    v = (v > p.thr) ? __fsub_rn(v, p.thr) : 0.f;
+                }
+                comp_add(F, v);
+                comp_add(Sx, __fmul_rn(v, static_cast<float>(x) - cc));
+                comp_add(Sy, __fmul_rn(v, static_cast<float>(y) - cc));
+            }
+        }
+    }
+    comp_group_reduce<L>(F);
+    comp_group_reduce<L>(Sx);
+    comp_group_reduce<L>(Sy);
+    if (l == 0 && valid) {
+        const float f = F.s + F.c;
+        const float sx = Sx.s + Sx.c;
+        const float sy = Sy.s + Sy.c;
+        const bool ok = f > 0.f;
+        float* s_w = s_out + static_cast<size_t>(w) * 2 * p.n_valid;
+        s_w[i] = ok ? sx / f : 0.f;
+        s_w[p.n_valid + i] = ok ? sy / f : 0.f;
+    }
+}
+
+}  // namespace rtc_pixel
+
+// Pixel-stage arguments of a handle for one frame (defined in calib_cog.cu).
+rtc_pixel::PixelArgs pixel_args(const rtc_handle* h, const uint16_t* d_frame, float* d_s);

@@ -121,18 +121,28 @@ int apply_subaps(rtc_handle* h, const std::vector<int32_t>& rc) {
     return RTC_OK;
 }
 
+}  // namespace
+
+int fail_handle(rtc_handle* h, int code, const char* msg) { return fail(h, code, "%s", msg); }
+
 // Read (and clear) the device status word after the stream has drained.
+
 int take_status(rtc_handle* h, cudaStream_t st) {
     RTC_CUDA(h, cudaMemcpyAsync(h->h_status, h->d_status, sizeof(int), cudaMemcpyDeviceToHost, st));
     RTC_CUDA(h, cudaStreamSynchronize(st));
     const int code = *h->h_status;
     if (code != 0) {
+        // an aborted launch may leave the grid-barrier count short: start it afresh
+        RTC_CUDA(h, cudaMemsetAsync(h->d_gridbar, 0, sizeof(unsigned long long), st));
+        h->grid_epoch = 0;
         RTC_CUDA(h, cudaMemsetAsync(h->d_status, 0, sizeof(int), st));
         RTC_CUDA(h, cudaStreamSynchronize(st));
         return fail(h, code, "a bounded device wait expired (results of this step are invalid)");
     }
     return RTC_OK;
 }
+
+namespace {
 
 int check_ready(rtc_handle* h) {
     if (!h) return RTC_EINVAL;
@@ -143,8 +153,7 @@ int check_ready(rtc_handle* h) {
 
 int enqueue_step(rtc_handle* h, const uint16_t* d_frame, float* d_dm_out, float* d_slopes_out,
                  cudaStream_t st) {
-    RTC_CUDA(h, launch_calib_cog(h, d_frame, h->d_s, st));
-    RTC_CUDA(h, launch_mvm_integrate(h, h->d_s, d_dm_out, st));
+    RTC_CUDA(h, launch_frame(h, d_frame, d_dm_out, st));
     if (d_slopes_out)
         RTC_CUDA(h, cudaMemcpyAsync(d_slopes_out, h->d_s, h->nslopes * sizeof(float),
                                     cudaMemcpyDeviceToDevice, st));
@@ -193,7 +202,8 @@ int rtc_create(const rtc_config* cfg, rtc_handle** out) {
     int rcode = RTC_OK;
     cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, c.device);
     if (h->num_sms < 1) h->num_sms = 1;
-    if (mvm_stream_configure() != cudaSuccess) {
+    if (mvm_stream_configure() != cudaSuccess || frame_kernel_configure() != cudaSuccess ||
+        loop_kernel_configure() != cudaSuccess) {
         rcode = fail(nullptr, RTC_EDEVICE, "cannot configure the reconstruction kernel");
     } else if (cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking) != cudaSuccess) {
         rcode = fail(nullptr, RTC_EDEVICE, "cudaStreamCreate failed");
@@ -205,11 +215,13 @@ int rtc_create(const rtc_config* cfg, rtc_handle** out) {
             cudaMalloc(&h->d_count, nrb * sizeof(unsigned)) != cudaSuccess ||
             cudaMalloc(&h->d_frame, frame_elems * sizeof(uint16_t)) != cudaSuccess ||
             cudaMalloc(&h->d_status, sizeof(int)) != cudaSuccess ||
+            cudaMalloc(&h->d_gridbar, sizeof(unsigned long long)) != cudaSuccess ||
             cudaMallocHost(&h->h_status, sizeof(int)) != cudaSuccess) {
             rcode = fail(nullptr, RTC_ENOMEM, "device allocation failed");
         } else if (cudaMemset(h->d_a, 0, c.nact * sizeof(float)) != cudaSuccess ||
                    cudaMemset(h->d_count, 0, nrb * sizeof(unsigned)) != cudaSuccess ||
-                   cudaMemset(h->d_status, 0, sizeof(int)) != cudaSuccess) {
+                   cudaMemset(h->d_status, 0, sizeof(int)) != cudaSuccess ||
+                   cudaMemset(h->d_gridbar, 0, sizeof(unsigned long long)) != cudaSuccess) {
             rcode = fail(nullptr, RTC_EDEVICE, "cudaMemset failed");
         } else {
             rcode = apply_subaps(h, default_subaps(c.nsub, c.obs));
@@ -239,6 +251,14 @@ int rtc_destroy(rtc_handle* h) {
     free_dev(h->d_count);
     free_dev(h->d_frame);
     free_dev(h->d_status);
+    free_dev(h->d_gridbar);
+    free_dev(h->d_sbuf);
+    free_dev(h->d_donectr);
+    free_dev(h->d_tseen);
+    if (h->h_ring) cudaFreeHost(h->h_ring);
+    if (h->h_seq) cudaFreeHost(h->h_seq);
+    if (h->h_dm_ring) cudaFreeHost(h->h_dm_ring);
+    if (h->h_done) cudaFreeHost(h->h_done);
     if (h->h_status) cudaFreeHost(h->h_status);
     h->h_status = nullptr;
     if (h->stream) cudaStreamDestroy(h->stream);

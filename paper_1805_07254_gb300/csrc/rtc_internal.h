@@ -17,6 +17,25 @@ constexpr int kMvmRows = 4;
 // Largest split-K factor (partials per actuator summed by the fixed-order tree).
 constexpr int kMaxKsplit = 32;
 
+// Completion record of one loop frame, written by the device into mapped host memory.
+struct rtc_loop_done {
+    unsigned long long seq;      // k + 1 once frame k's DM commands are in host memory
+    unsigned long long t_seen;   // device %globaltimer when the frame's flag was seen
+    unsigned long long t_done;   // device %globaltimer when the last block finished
+    unsigned long long pad;
+};
+
+// Device-visible addresses of the host ring for one rtc_run_loop call.
+struct LoopLaunch {
+    const uint16_t* d_frames;
+    unsigned long long frame_elems;
+    const unsigned long long* d_seq;
+    float* d_dm;
+    rtc_loop_done* d_done;
+    unsigned long long n_frames;
+    int nslot;
+};
+
 struct rtc_handle {
     rtc_config cfg{};
     int side = 0;               // frame side in pixels (nsub * npx)
@@ -47,6 +66,18 @@ struct rtc_handle {
     unsigned* d_count = nullptr;    // [ceil(nact/kMvmRows)] arrival counters (scratch, self-resetting)
     uint16_t* d_frame = nullptr;    // [n_wfs][side][side] staging for host frames
     int* d_status = nullptr;        // device-side error word (RTC_ETIMEDOUT from bounded waits)
+    unsigned long long* d_gridbar = nullptr;  // grid-barrier arrival counter (only grows)
+    unsigned long long grid_epoch = 0;        // fused launches issued against d_gridbar
+
+    // persistent loop (allocated by the first rtc_run_loop)
+    float* d_sbuf = nullptr;                  // [2][kpad] slope vectors by frame parity
+    unsigned long long* d_donectr = nullptr;  // finished-block counter
+    unsigned long long* d_tseen = nullptr;    // [2] device time each frame was seen
+    uint16_t* h_ring = nullptr;               // pinned mapped [RTC_LOOP_SLOTS][n_wfs][H][W]
+    unsigned long long* h_seq = nullptr;      // pinned mapped [RTC_LOOP_SLOTS]
+    float* h_dm_ring = nullptr;               // pinned mapped [RTC_LOOP_SLOTS][nact]
+    rtc_loop_done* h_done = nullptr;          // pinned mapped [RTC_LOOP_SLOTS]
+    int sbuf_kpad = -1;                       // kpad d_sbuf was sized for
     int* h_status = nullptr;        // pinned host mirror of d_status
 
     std::string err;
@@ -61,6 +92,16 @@ cudaError_t launch_calib_cog(const rtc_handle* h, const uint16_t* d_frame, float
 // the leaky integrator; d_partial holds shared-row-group partials, d_count their
 // self-resetting arrival counters.
 cudaError_t mvm_stream_configure();
+cudaError_t launch_decay(const rtc_handle* h, float* d_dm_out, cudaStream_t st);
+
+// Fused frame kernel (pixel stage + grid barrier + streaming MVM + integrator),
+// one cooperative launch per frame; the slopes land in h->d_s.
+cudaError_t frame_kernel_configure();
+
+// Persistent loop kernel (see loop_kernel.cu).
+cudaError_t loop_kernel_configure();
+cudaError_t launch_loop(rtc_handle* h, const LoopLaunch& ll, cudaStream_t st);
+cudaError_t launch_frame(rtc_handle* h, const uint16_t* d_frame, float* d_dm_out, cudaStream_t st);
 cudaError_t launch_mvm_integrate(const rtc_handle* h, const float* d_s, float* d_dm_out,
                                  cudaStream_t st);
 
@@ -74,6 +115,11 @@ cudaError_t launch_mvm_raw(int store, const void* d_M, const float* d_scale, int
 // Convert an FP32 device matrix [nact][K] into the stored layout [nact][kpad].
 cudaError_t launch_quantise(int store, const float* d_src, int nact, int K, int kpad,
                             void* d_dst, float* d_scale, cudaStream_t st);
+
+// Read and clear the device status word after `st` drains (RTC_OK or the recorded
+// error, which also restarts the grid-barrier count); set the handle's message.
+int take_status(rtc_handle* h, cudaStream_t st);
+int fail_handle(rtc_handle* h, int code, const char* msg);
 
 // Message returned by rtc_last_error(NULL) for failures of calls without a handle.
 void rtc_set_global_error(const char* msg);

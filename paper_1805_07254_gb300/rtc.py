@@ -34,6 +34,24 @@ class RtcInfo(C.Structure):
                 ("matrix_bytes", C.c_int64), ("frame_bytes", C.c_int64), ("calib_bytes", C.c_int64)]
 
 
+SOURCE_FN = C.CFUNCTYPE(C.c_int, C.c_void_p, C.c_uint64, C.c_void_p)
+SINK_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_uint64, C.POINTER(C.c_float))
+LOOP_SLOTS = 8
+
+
+class RtcLoopConfig(C.Structure):
+    _fields_ = [("n_frames", C.c_uint64), ("rate_hz", C.c_double), ("source", SOURCE_FN),
+                ("source_user", C.c_void_p), ("preload", C.c_void_p), ("n_preload", C.c_int32),
+                ("sink", SINK_FN), ("sink_user", C.c_void_p), ("e2e_ns", C.c_void_p),
+                ("dev_ns", C.c_void_p)]
+
+
+class RtcStats(C.Structure):
+    _fields_ = [("frames", C.c_uint64), ("frames_per_s", C.c_double)] + [
+        (f"{a}_{b}", C.c_double) for a in ("e2e", "dev")
+        for b in ("p50_us", "p99_us", "p999_us", "mean_us", "rms_jitter_us", "p2p_us")]
+
+
 _P = C.c_void_p
 _I = C.c_int
 # name -> (restype, argtypes); mirrors include/rtc.h
@@ -57,6 +75,7 @@ SIGNATURES = {
     "rtc_reconstruct_async": (_I, [_P, _P, _P, _P]),
     "rtc_mvm_integrate_noalloc": (_I, [_P, C.c_int32, _P, C.c_int32, C.c_int32, _P, _P, _P,
                                        C.c_float, C.c_float, C.c_int32, _P]),
+    "rtc_run_loop": (_I, [_P, C.POINTER(RtcLoopConfig), C.POINTER(RtcStats)]),
 }
 
 _lib = None
@@ -224,6 +243,64 @@ class Rtc:
         """Enqueue MVM + integrator from ``d_slopes`` (None: the resident slope buffer)."""
         self._check(self._lib.rtc_reconstruct_async(self._h, _ptr(d_slopes), _ptr(d_dm_out),
                                                     _stream_ptr(stream)))
+
+    def run_loop(self, n_frames: int, rate_hz: float = 0.0, frames=None, source=None, sink=None,
+                 record: bool = True):
+        """Persistent real-time loop (rtc_run_loop).
+
+        frames: uint16 array (n, [n_wfs,] H, W), 1 <= n <= 8, cycled; or source(k) -> frame
+        array for frame k (None stops the loop).  sink(k, dm) receives each frame's DM
+        commands (a float32 array valid during the call).  Returns (stats dict, e2e_ns,
+        dev_ns) with per-frame latencies when record is true."""
+        n_frames = int(n_frames)
+        cfg = RtcLoopConfig()
+        cfg.n_frames = n_frames
+        cfg.rate_hz = float(rate_hz)
+        keep = []
+        if source is not None:
+            nbytes = [None]
+
+            def _src(user, k, dst):
+                try:
+                    f = source(int(k))
+                    if f is None:
+                        return 1
+                    f = np.ascontiguousarray(f, dtype=np.uint16)
+                    C.memmove(dst, f.ctypes.data, f.nbytes)
+                    return 0
+                except Exception:          # a failing source ends the loop
+                    return 1
+            cfg.source = SOURCE_FN(_src)
+            keep.append(cfg.source)
+        else:
+            if frames is None:
+                raise ValueError("give frames or a source")
+            fr = np.ascontiguousarray(frames, dtype=np.uint16)
+            cfg.preload = fr.ctypes.data
+            cfg.n_preload = fr.shape[0]
+            keep.append(fr)
+        if sink is not None:
+            nact = self.cfg.nact
+
+            def _sink(user, k, dm):
+                sink(int(k), np.ctypeslib.as_array(dm, shape=(nact,)).copy())
+            cfg.sink = SINK_FN(_sink)
+            keep.append(cfg.sink)
+        e2e = dev = None
+        if record:
+            e2e = np.zeros(n_frames, np.int64)
+            dev = np.zeros(n_frames, np.int64)
+            cfg.e2e_ns = e2e.ctypes.data
+            cfg.dev_ns = dev.ctypes.data
+        st = RtcStats()
+        rc = self._lib.rtc_run_loop(self._h, C.byref(cfg), C.byref(st))
+        stats = {k: getattr(st, k) for k, _ in RtcStats._fields_}
+        if rc != RTC_OK:
+            err = RtcError(rc, self._lib.rtc_last_error(self._h).decode())
+            err.stats = stats
+            raise err
+        n = int(st.frames)
+        return stats, (e2e[:n] if record else None), (dev[:n] if record else None)
 
     def synchronize(self, stream=None):
         self._check(self._lib.rtc_synchronize(self._h, _stream_ptr(stream)))

@@ -1,0 +1,122 @@
+"""The persistent real-time loop (rtc_run_loop) against the per-frame path and the
+FP64 oracle; pacing, early stop, and the bounded frame wait."""
+import time
+
+import numpy as np
+import pytest
+import torch
+
+import synth
+from helpers import make_pair, rel_rms
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    import __graft_entry__ as g
+    g.build()
+
+
+def _per_frame_reference(r, frames, n):
+    """DM commands of frames[k % len(frames)], k < n, through the fused per-frame kernel."""
+    dev = torch.device("cuda:0")
+    st = torch.cuda.current_stream()
+    d_dm = torch.empty(r.cfg.nact, device=dev)
+    out = []
+    for k in range(n):
+        r.process_frame_async(torch.from_numpy(frames[k % len(frames)]).to(dev), d_dm, stream=st)
+        r.synchronize(st)
+        out.append(d_dm.cpu().numpy().copy())
+    return out
+
+
+@pytest.mark.parametrize("store", ["f32", "bf16", "fp8"])
+def test_loop_equals_per_frame_path(store):
+    cfg = synth.elt_scao()
+    frames, _ = synth.make_frames(cfg, 0, 4)
+    frames = frames.numpy()
+    n = 12
+    r1, *_ = make_pair(cfg, store=store)
+    r2, *_ = make_pair(cfg, store=store)
+    got = {}
+    stats, e2e, dev = r1.run_loop(n, frames=frames, sink=lambda k, dm: got.__setitem__(k, dm))
+    assert stats["frames"] == n and len(got) == n
+    ref = _per_frame_reference(r2, frames, n)
+    for k in range(n):
+        np.testing.assert_array_equal(got[k], ref[k])
+    np.testing.assert_array_equal(r1.get_dm(), ref[-1])
+    assert np.all(e2e > 0) and np.all(dev > 0) and np.all(dev <= e2e)
+
+
+def test_loop_tiny_against_oracle():
+    cfg = synth.tiny_scao()
+    frames, _ = synth.make_frames(cfg, 0, 8)
+    frames = frames.numpy()
+    n = 64
+    r, oracle, *_ = make_pair(cfg)
+    got = {}
+    r.run_loop(n, frames=frames, sink=lambda k, dm: got.__setitem__(k, dm))
+    for k in range(n):
+        a_ref, _ = oracle.step(frames[k % len(frames)])
+        assert rel_rms(got[k], a_ref) <= 1e-5, k
+
+
+def test_loop_source_callback_stop_and_continue():
+    cfg = synth.tiny_scao()
+    frames, _ = synth.make_frames(cfg, 0, 7)
+    frames = frames.numpy()
+    r, oracle, *_ = make_pair(cfg)
+
+    def source(k):
+        return frames[k] if k < 5 else None          # the source ends after 5 frames
+
+    got = {}
+    stats, e2e, dev = r.run_loop(20, source=source, sink=lambda k, dm: got.__setitem__(k, dm))
+    assert stats["frames"] == 5 and len(e2e) == 5
+    for k in range(5):
+        a_ref, _ = oracle.step(frames[k])
+        assert rel_rms(got[k], a_ref) <= 1e-5
+    # the integrator carries on in the per-frame path
+    dm = r.process_frame(frames[5])
+    a_ref, _ = oracle.step(frames[5])
+    assert rel_rms(dm, a_ref) <= 1e-5
+
+
+def test_loop_paced_rate_and_stats():
+    cfg = synth.tiny_scao()
+    frames, _ = synth.make_frames(cfg, 0, 2)
+    r, *_ = make_pair(cfg)
+    stats, e2e, dev = r.run_loop(200, rate_hz=2000.0, frames=frames.numpy())
+    assert stats["frames"] == 200
+    assert 1600.0 <= stats["frames_per_s"] <= 2100.0, stats["frames_per_s"]
+    for pre in ("e2e", "dev"):
+        assert 0 < stats[f"{pre}_p50_us"] <= stats[f"{pre}_p99_us"] <= stats[f"{pre}_p999_us"]
+        assert stats[f"{pre}_rms_jitter_us"] >= 0
+    assert abs(stats["e2e_p50_us"] - np.median(e2e) / 1e3) < 1.0
+
+
+def test_loop_frame_wait_times_out_and_context_survives():
+    """A frame that never comes: the kernel's bounded wait (2 s) expires, the call
+    returns RTC_ETIMEDOUT, and the handle keeps working."""
+    from paper_1805_07254_gb300.rtc import RtcError, RTC_ETIMEDOUT
+    cfg = synth.tiny_scao()
+    frames, _ = synth.make_frames(cfg, 0, 3)
+    frames = frames.numpy()
+    r, oracle, *_ = make_pair(cfg)
+
+    def slow_source(k):
+        if k == 2:
+            time.sleep(3.0)                          # longer than the device's frame wait
+        return frames[k % 3]
+
+    t0 = time.time()
+    with pytest.raises(RtcError) as e:
+        r.run_loop(4, source=slow_source)
+    assert e.value.code == RTC_ETIMEDOUT
+    assert time.time() - t0 < 15
+    r.reset()
+    oracle.a[:] = 0
+    dm = r.process_frame(frames[0])
+    a_ref, _ = oracle.step(frames[0])
+    assert rel_rms(dm, a_ref) <= 1e-5

@@ -200,3 +200,28 @@ def test_stress_six_wfs_fp8_sampled_rows():
     q, sc = Q.fp8_row_quantise(M[rows])
     ref = cfg.gain * ((sc.astype(np.float64)[:, None] * q) @ s_ref)
     assert rel_rms(dm[rows], ref) <= DM_TOL
+
+
+@pytest.mark.parametrize("store", ["f32", "bf16", "fp8"])
+def test_fused_frame_kernel_equals_stage_kernels(store):
+    """rtc_process_frame_async (one fused cooperative kernel) and the two stage calls
+    (rtc_centroid_async + rtc_reconstruct_async) give identical slopes and commands."""
+    cfg = synth.elt_scao()
+    frames, _ = synth.make_frames(cfg, 0, 3)
+    r1, _, *_ = make_pair(cfg, store=store)
+    r2, _, *_ = make_pair(cfg, store=store)
+    dev = torch.device("cuda:0")
+    st = torch.cuda.current_stream()
+    dm1 = torch.empty(cfg.nact, device=dev)
+    dm2 = torch.empty(cfg.nact, device=dev)
+    s1 = torch.empty(cfg.nslopes, device=dev)
+    s2 = torch.empty(cfg.nslopes, device=dev)
+    for k in range(frames.shape[0]):
+        d_frame = frames[k].contiguous().to(dev)
+        r1.process_frame_async(d_frame, dm1, s1, stream=st)
+        r2.centroid_async(d_frame, s2, stream=st)
+        r2.reconstruct_async(None, dm2, stream=st)
+        r1.synchronize(st)
+        r2.synchronize(st)
+        assert torch.equal(s1, s2)
+        assert torch.equal(dm1, dm2)
