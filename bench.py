@@ -50,6 +50,8 @@ def parse_args(argv=None):
     ap.add_argument("--store", choices=["f32", "bf16", "fp8"], default="f32")
     ap.add_argument("--ksplit", type=int, default=0)
     ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--no-loop", action="store_true")
+    ap.add_argument("--loop-frames", type=int, default=2000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-s", type=float, default=15.0)
     ap.add_argument("--reference-budget-s", type=float, default=150.0)
@@ -370,6 +372,26 @@ def ours(args):
                                "stage_mvm_hbm_gbs": round(mb / (mv["mean"] * 1e-6) / 1e9, 1)}
             rv.close()
 
+    # persistent real-time loop (rtc_run_loop): frames published by a host thread into
+    # pinned mapped memory, DM commands back in host memory; paced at 1 kHz and flat out
+    loop = {}
+    if not args.no_loop:
+        for store, mode, rate, n in (("f32", "1kHz", 1000.0, args.loop_frames),
+                                     ("f32", "max", 0.0, 5 * args.loop_frames),
+                                     ("bf16", "max", 0.0, 5 * args.loop_frames),
+                                     ("fp8", "max", 0.0, 5 * args.loop_frames)):
+            rl = controller(store)
+            st_l, _, _ = rl.run_loop(n, rate_hz=rate, frames=frames[:8])
+            loop[f"{store}_{mode}"] = {
+                "frames": int(st_l["frames"]), "frames_per_s": round(st_l["frames_per_s"], 1),
+                "e2e_p50_us": round(st_l["e2e_p50_us"], 2), "e2e_p99_us": round(st_l["e2e_p99_us"], 2),
+                "e2e_p999_us": round(st_l["e2e_p999_us"], 2),
+                "e2e_rms_jitter_us": round(st_l["e2e_rms_jitter_us"], 3),
+                "e2e_p2p_us": round(st_l["e2e_p2p_us"], 2),
+                "dev_p50_us": round(st_l["dev_p50_us"], 2), "dev_p99_us": round(st_l["dev_p99_us"], 2),
+                "dev_rms_jitter_us": round(st_l["dev_rms_jitter_us"], 3)}
+            rl.close()
+
     # max over ranks (worst replica)
     value = s_step["p50"]
     if world > 1:
@@ -411,6 +433,7 @@ def ours(args):
         "clocks": clocks,
         "timed_wall_s_incl_flush": round(t_wall, 3),
         "variants": variants,
+        "loop": loop,
         "cpu_baseline": cpu,
     }
     if rank == 0:

@@ -232,6 +232,78 @@ typedef struct rtc_stats {
  * RTC_EDEVICE, RTC_ETIMEDOUT. */
 int rtc_run_loop(rtc_handle* h, const rtc_loop_config* cfg, rtc_stats* stats);
 
+/* ---- learned slope predictor --------------------------------------------------
+ * An addition to the paper's pipeline: a shared MLP predicts each subaperture's
+ * next slopes from its 5x5 neighbourhood over the last 4 frames, to offset the
+ * integrator's one-frame servo lag.  Definition (both the kernels and the FP64
+ * oracle follow it):
+ *   features  x_f, f = ((lag*2 + axis)*5 + (dr+2))*5 + (dc+2), 200 values: the
+ *             slope (axis 0 = x, 1 = y) of the neighbour at grid offset (dr, dc)
+ *             in the frame `lag` frames ago (0 = newest), divided by sigma; 0 off
+ *             the grid or off the pupil;
+ *   network   z1 = W1 x + b1, h1 = GELU(z1), z2 = W2 h1 + b2, h2 = GELU(z2),
+ *             y = W3 h2 + b3; 200 -> 64 -> 64 -> 2; exact GELU z*Phi(z);
+ *   output    predicted next slopes = s_k + sigma * y;
+ *   loss      sum over the batch of |y - t|^2 / (2B), t = (s_{k+1} - s_k) / sigma;
+ *   update    Adam (beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected).
+ * Parameters are one float32 vector of RTC_MLP_NPARAMS values: W1 [64][200],
+ * b1 [64], W2 [64][64], b2 [64], W3 [2][64], b3 [2], each row-major.  The GEMMs
+ * run on the tensor cores with BF16 operands and FP32 accumulation; the master
+ * weights and Adam state are FP32. */
+
+#define RTC_MLP_NPARAMS 17154
+#define RTC_MLP_NFEAT 200
+
+typedef struct rtc_mlp rtc_mlp;
+
+/* A network on `device` with all parameters zero.  Errors: RTC_EINVAL, RTC_ENOMEM. */
+int rtc_mlp_create(int32_t device, rtc_mlp** out);
+int rtc_mlp_destroy(rtc_mlp* m);
+
+/* Host float32 [RTC_MLP_NPARAMS] in/out; setting resets the Adam state and step. */
+int rtc_mlp_set_params(rtc_mlp* m, const float* params, int64_t n);
+int rtc_mlp_get_params(rtc_mlp* m, float* params, int64_t n);
+
+/* Subaperture geometry used by rtc_mlp_train_seq: host int32 [n_valid][2] (row,
+ * col), row-major order, on an nsub x nsub grid.  Errors: RTC_EINVAL. */
+int rtc_mlp_set_geometry(rtc_mlp* m, const int32_t* rc, int32_t n_valid, int32_t nsub);
+
+/* y = net(X) for device X float32 [B][200] -> device Y float32 [B][2]. */
+int rtc_mlp_forward(rtc_mlp* m, const float* d_X, int32_t B, float* d_Y, void* stream);
+
+/* Gradient of the loss at the current parameters for the batch (X [B][200],
+ * targets T [B][2], device): d_grad float32 [RTC_MLP_NPARAMS] (device), d_loss
+ * float32 [1] (device, may be NULL).  No update. */
+int rtc_mlp_gradient(rtc_mlp* m, const float* d_X, const float* d_T, int32_t B, float* d_grad,
+                     float* d_loss, void* stream);
+
+/* One Adam step with learning rate lr on the batch; d_loss (device, may be NULL)
+ * receives the batch loss before the step. */
+int rtc_mlp_train_step(rtc_mlp* m, const float* d_X, const float* d_T, int32_t B, float lr,
+                       float* d_loss, void* stream);
+
+/* One Adam step on samples drawn from a slope sequence: d_S device float32
+ * [n_frames][2 n_valid] (x block then y block per frame), d_samples device int32
+ * [B][2] of (subaperture, frame k) with 3 <= k <= n_frames - 2.  Features come
+ * from frames k..k-3, targets from k+1.  Needs rtc_mlp_set_geometry. */
+int rtc_mlp_train_seq(rtc_mlp* m, const float* d_S, int32_t n_frames, const int32_t* d_samples,
+                      int32_t B, float sigma, float lr, float* d_loss, void* stream);
+
+/* Predictions over a slope sequence (geometry from rtc_mlp_set_geometry): for
+ * every frame k with 3 <= k <= n_frames - 2, row k + 1 of d_out (device float32
+ * [n_frames][2 n_valid]) receives s_k + sigma * y from the features of frames
+ * k..k-3 of d_S; other rows are not written. */
+int rtc_mlp_predict_seq(rtc_mlp* m, const float* d_S, int32_t n_frames, float sigma, float* d_out,
+                        void* stream);
+
+/* Use a predictor in the per-frame path of a handle (SCAO only, n_wfs == 1):
+ * params host float32 [RTC_MLP_NPARAMS], sigma the slope scale of the features.
+ * The handle keeps the last 4 measured slope vectors; with the predictor on, the
+ * reconstruction uses the predicted next slopes instead of the measured ones.
+ * rtc_reset clears the history.  Errors: RTC_EINVAL, RTC_ENOMEM, RTC_EDEVICE. */
+int rtc_load_predictor(rtc_handle* h, const float* params, int64_t n, float sigma);
+int rtc_set_predictor(rtc_handle* h, int32_t on);
+
 /* Largest sizes rtc_mvm_integrate_noalloc accepts (its scratch is fixed at load). */
 #define RTC_NOALLOC_MAX_NACT   8192
 #define RTC_NOALLOC_MAX_KSPLIT 16

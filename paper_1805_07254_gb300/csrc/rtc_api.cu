@@ -11,6 +11,7 @@
 #include <string>
 #include <vector>
 
+#include "mlp.h"
 #include "rtc_internal.h"
 
 namespace {
@@ -51,6 +52,18 @@ template <typename T>
 void free_dev(T*& p) {
     if (p) cudaFree(p);
     p = nullptr;
+}
+
+void free_predictor(rtc_handle* h) {
+    if (h->pred) {
+        mlp_free(*h->pred);
+        delete h->pred;
+        h->pred = nullptr;
+    }
+    free_dev(h->d_nbr);
+    free_dev(h->d_ring);
+    free_dev(h->d_spred);
+    h->pred_on = false;
 }
 
 int dtype_size(int dt) {
@@ -100,6 +113,7 @@ int apply_subaps(rtc_handle* h, const std::vector<int32_t>& rc) {
                 return fail(h, RTC_EINVAL, "subap map must be strictly increasing in row-major order (entry %d)", i);
         }
     }
+    free_predictor(h);        // its neighbour table and history depend on the map
     free_dev(h->d_rc);
     free_dev(h->d_dark);
     free_dev(h->d_gainmap);
@@ -153,6 +167,22 @@ int check_ready(rtc_handle* h) {
 
 int enqueue_step(rtc_handle* h, const uint16_t* d_frame, float* d_dm_out, float* d_slopes_out,
                  cudaStream_t st) {
+    if (h->pred_on && h->kpad > 0) {
+        // measured slopes into the history ring, predicted next slopes, then the
+        // reconstruction from the prediction
+        const int head = (h->ring_head + 1) & 3;
+        float* s_meas = h->d_ring + static_cast<size_t>(head) * h->kpad;
+        RTC_CUDA(h, launch_calib_cog(h, d_frame, s_meas, st));
+        RTC_CUDA(h, mlp_launch_predict(*h->pred, h->d_ring, h->kpad, head, h->n_valid, h->d_nbr,
+                                       h->pred_sigma, h->d_spred, st));
+        RTC_CUDA(h, launch_mvm_integrate(h, h->d_spred, d_dm_out, st));
+        h->ring_head = head;
+        RTC_CUDA(h, cudaMemcpyAsync(h->d_s, s_meas, h->kpad * sizeof(float), cudaMemcpyDeviceToDevice, st));
+        if (d_slopes_out)
+            RTC_CUDA(h, cudaMemcpyAsync(d_slopes_out, s_meas, h->nslopes * sizeof(float),
+                                        cudaMemcpyDeviceToDevice, st));
+        return RTC_OK;
+    }
     RTC_CUDA(h, launch_frame(h, d_frame, d_dm_out, st));
     if (d_slopes_out)
         RTC_CUDA(h, cudaMemcpyAsync(d_slopes_out, h->d_s, h->nslopes * sizeof(float),
@@ -240,6 +270,7 @@ int rtc_destroy(rtc_handle* h) {
     if (!h) return RTC_OK;
     DeviceScope ds(h->cfg.device);
     if (h->stream) cudaStreamSynchronize(h->stream);
+    free_predictor(h);
     free_dev(h->d_rc);
     free_dev(h->d_dark);
     free_dev(h->d_gainmap);
@@ -380,7 +411,54 @@ int rtc_reset(rtc_handle* h) {
     if (!h) return RTC_EINVAL;
     DeviceScope ds(h->cfg.device);
     RTC_CUDA(h, cudaMemsetAsync(h->d_a, 0, h->cfg.nact * sizeof(float), h->stream));
+    if (h->d_ring)
+        RTC_CUDA(h, cudaMemsetAsync(h->d_ring, 0, 4 * static_cast<size_t>(h->kpad) * sizeof(float), h->stream));
+    h->ring_head = 3;
     RTC_CUDA(h, cudaStreamSynchronize(h->stream));
+    return RTC_OK;
+}
+
+int rtc_load_predictor(rtc_handle* h, const float* params, int64_t n, float sigma) {
+    if (!h) return RTC_EINVAL;
+    if (!params || n != RTC_MLP_NPARAMS || !(sigma > 0.f) || !isfinite(sigma))
+        return fail(h, RTC_EINVAL, "need RTC_MLP_NPARAMS parameters and sigma > 0");
+    if (h->cfg.n_wfs != 1) return fail(h, RTC_EINVAL, "the predictor is for single-WFS handles");
+    for (int64_t i = 0; i < n; ++i)
+        if (!isfinite(params[i])) return fail(h, RTC_EINVAL, "parameters must be finite");
+    DeviceScope ds(h->cfg.device);
+    RTC_CUDA(h, cudaStreamSynchronize(h->stream));
+    free_predictor(h);
+    RTC_CUDA(h, mlp_configure());
+    h->pred = new MlpDev();
+    if (mlp_alloc(*h->pred) != RTC_OK) {
+        free_predictor(h);
+        return fail(h, RTC_ENOMEM, "cannot allocate the predictor");
+    }
+    if (mlp_upload(*h->pred, params, h->stream) != RTC_OK) {
+        free_predictor(h);
+        return fail(h, RTC_EDEVICE, "predictor upload failed");
+    }
+    const std::vector<int> nbr = mlp_neighbours(h->rc.data(), h->n_valid, h->cfg.nsub);
+    const size_t ring = 4 * static_cast<size_t>(std::max(h->kpad, 16)) * sizeof(float);
+    if ((!nbr.empty() && cudaMalloc(&h->d_nbr, nbr.size() * sizeof(int)) != cudaSuccess) ||
+        cudaMalloc(&h->d_ring, ring) != cudaSuccess ||
+        cudaMalloc(&h->d_spred, std::max(h->kpad, 16) * sizeof(float)) != cudaSuccess) {
+        free_predictor(h);
+        return fail(h, RTC_ENOMEM, "cannot allocate the predictor state");
+    }
+    if (!nbr.empty())
+        RTC_CUDA(h, cudaMemcpy(h->d_nbr, nbr.data(), nbr.size() * sizeof(int), cudaMemcpyHostToDevice));
+    RTC_CUDA(h, cudaMemset(h->d_ring, 0, ring));
+    RTC_CUDA(h, cudaMemset(h->d_spred, 0, std::max(h->kpad, 16) * sizeof(float)));
+    h->ring_head = 3;
+    h->pred_sigma = sigma;
+    return RTC_OK;
+}
+
+int rtc_set_predictor(rtc_handle* h, int32_t on) {
+    if (!h) return RTC_EINVAL;
+    if (on && !h->pred) return fail(h, RTC_ESTATE, "no predictor loaded");
+    h->pred_on = on != 0;
     return RTC_OK;
 }
 

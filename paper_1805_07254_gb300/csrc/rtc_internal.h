@@ -78,6 +78,15 @@ struct rtc_handle {
     float* h_dm_ring = nullptr;               // pinned mapped [RTC_LOOP_SLOTS][nact]
     rtc_loop_done* h_done = nullptr;          // pinned mapped [RTC_LOOP_SLOTS]
     int sbuf_kpad = -1;                       // kpad d_sbuf was sized for
+
+    // learned slope predictor (rtc_load_predictor)
+    struct MlpDev* pred = nullptr;            // network weights on the device
+    bool pred_on = false;
+    float pred_sigma = 1.f;
+    int* d_nbr = nullptr;                     // [n_valid][25] neighbour table
+    float* d_ring = nullptr;                  // [4][kpad] last measured slope vectors
+    int ring_head = 3;                        // row of the newest vector
+    float* d_spred = nullptr;                 // [kpad] predicted slopes, zero padded
     int* h_status = nullptr;        // pinned host mirror of d_status
 
     std::string err;

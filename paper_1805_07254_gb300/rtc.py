@@ -76,6 +76,18 @@ SIGNATURES = {
     "rtc_mvm_integrate_noalloc": (_I, [_P, C.c_int32, _P, C.c_int32, C.c_int32, _P, _P, _P,
                                        C.c_float, C.c_float, C.c_int32, _P]),
     "rtc_run_loop": (_I, [_P, C.POINTER(RtcLoopConfig), C.POINTER(RtcStats)]),
+    "rtc_mlp_create": (_I, [C.c_int32, C.POINTER(_P)]),
+    "rtc_mlp_destroy": (_I, [_P]),
+    "rtc_mlp_set_params": (_I, [_P, _P, C.c_int64]),
+    "rtc_mlp_get_params": (_I, [_P, _P, C.c_int64]),
+    "rtc_mlp_set_geometry": (_I, [_P, _P, C.c_int32, C.c_int32]),
+    "rtc_mlp_forward": (_I, [_P, _P, C.c_int32, _P, _P]),
+    "rtc_mlp_gradient": (_I, [_P, _P, _P, C.c_int32, _P, _P, _P]),
+    "rtc_mlp_train_step": (_I, [_P, _P, _P, C.c_int32, C.c_float, _P, _P]),
+    "rtc_mlp_train_seq": (_I, [_P, _P, C.c_int32, _P, C.c_int32, C.c_float, C.c_float, _P, _P]),
+    "rtc_mlp_predict_seq": (_I, [_P, _P, C.c_int32, C.c_float, _P, _P]),
+    "rtc_load_predictor": (_I, [_P, _P, C.c_int64, C.c_float]),
+    "rtc_set_predictor": (_I, [_P, C.c_int32]),
 }
 
 _lib = None
@@ -302,6 +314,13 @@ class Rtc:
         n = int(st.frames)
         return stats, (e2e[:n] if record else None), (dev[:n] if record else None)
 
+    def load_predictor(self, params, sigma: float):
+        p = np.ascontiguousarray(params, dtype=np.float32).reshape(-1)
+        self._check(self._lib.rtc_load_predictor(self._h, _ptr(p), p.size, sigma))
+
+    def set_predictor(self, on: bool):
+        self._check(self._lib.rtc_set_predictor(self._h, 1 if on else 0))
+
     def synchronize(self, stream=None):
         self._check(self._lib.rtc_synchronize(self._h, _stream_ptr(stream)))
 
@@ -317,6 +336,70 @@ def mvm_integrate_noalloc(d_M, store: str, d_row_scales, nact: int, kpad: int, d
                                        _stream_ptr(stream))
     if rc != RTC_OK:
         raise RtcError(rc, lib.rtc_last_error(None).decode())
+
+
+MLP_NPARAMS = 17154
+
+
+class Mlp:
+    """The slope-predictor network (rtc_mlp_*): training and evaluation on device tensors."""
+
+    def __init__(self, device: int = 0, params=None):
+        self._lib = load_library()
+        h = _P()
+        self._check(self._lib.rtc_mlp_create(device, C.byref(h)))
+        self._h = h
+        if params is not None:
+            self.set_params(params)
+
+    def _check(self, rc):
+        if rc != RTC_OK:
+            raise RtcError(rc, self._lib.rtc_last_error(None).decode())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.rtc_mlp_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_params(self, params):
+        p = np.ascontiguousarray(params, dtype=np.float32).reshape(-1)
+        self._check(self._lib.rtc_mlp_set_params(self._h, _ptr(p), p.size))
+
+    def get_params(self) -> np.ndarray:
+        out = np.empty(MLP_NPARAMS, np.float32)
+        self._check(self._lib.rtc_mlp_get_params(self._h, _ptr(out), out.size))
+        return out
+
+    def set_geometry(self, rc, nsub: int):
+        rc = np.ascontiguousarray(rc, dtype=np.int32).reshape(-1, 2)
+        self._check(self._lib.rtc_mlp_set_geometry(self._h, _ptr(rc), rc.shape[0], nsub))
+
+    def forward(self, d_X, d_Y, stream=None):
+        self._check(self._lib.rtc_mlp_forward(self._h, _ptr(d_X), d_X.shape[0], _ptr(d_Y),
+                                              _stream_ptr(stream)))
+
+    def gradient(self, d_X, d_T, d_grad, d_loss=None, stream=None):
+        self._check(self._lib.rtc_mlp_gradient(self._h, _ptr(d_X), _ptr(d_T), d_X.shape[0],
+                                               _ptr(d_grad), _ptr(d_loss), _stream_ptr(stream)))
+
+    def train_step(self, d_X, d_T, lr: float, d_loss=None, stream=None):
+        self._check(self._lib.rtc_mlp_train_step(self._h, _ptr(d_X), _ptr(d_T), d_X.shape[0], lr,
+                                                 _ptr(d_loss), _stream_ptr(stream)))
+
+    def train_seq(self, d_S, d_samples, sigma: float, lr: float, d_loss=None, stream=None):
+        self._check(self._lib.rtc_mlp_train_seq(self._h, _ptr(d_S), d_S.shape[0], _ptr(d_samples),
+                                                d_samples.shape[0], sigma, lr, _ptr(d_loss),
+                                                _stream_ptr(stream)))
+
+    def predict_seq(self, d_S, sigma: float, d_out, stream=None):
+        self._check(self._lib.rtc_mlp_predict_seq(self._h, _ptr(d_S), d_S.shape[0], sigma,
+                                                  _ptr(d_out), _stream_ptr(stream)))
 
 
 def version() -> str:
