@@ -372,6 +372,22 @@ def ours(args):
                                "stage_mvm_hbm_gbs": round(mb / (mv["mean"] * 1e-6) / 1e9, 1)}
             rv.close()
 
+    # reduced precision + learned predictor: BF16 matrix, predictor on (pixel kernel,
+    # predictor kernel, streaming reconstruction); the weights do not change the timing
+    if not args.no_variants:
+        from synth.mlp_init import init_mlp_params, flatten
+        rp = controller("bf16")
+        rp.load_predictor(flatten(init_mlp_params(0)), 0.3)
+        rp.set_predictor(True)
+        (s3,) = time_steps(torch, rp, d_frames, d_dm, flush, st, min(args.steps, 2000),
+                           args.warmup, fused=True)
+        sp = stats_us(s3)
+        variants["bf16_predictor"] = {"p50_us": round(sp["p50"], 3), "p99_us": round(sp["p99"], 3),
+                                      "p999_us": round(sp["p999"], 3),
+                                      "rms_jitter_us": round(sp["rms_jitter"], 3),
+                                      "kernels_per_frame": 3}
+        rp.close()
+
     # persistent real-time loop (rtc_run_loop): frames published by a host thread into
     # pinned mapped memory, DM commands back in host memory; paced at 1 kHz and flat out
     loop = {}

@@ -232,6 +232,44 @@ typedef struct rtc_stats {
  * RTC_EDEVICE, RTC_ETIMEDOUT. */
 int rtc_run_loop(rtc_handle* h, const rtc_loop_config* cfg, rtc_stats* stats);
 
+/* ---- serving several loops on one GPU (continuous batching) --------------------
+ * A server runs independent controllers (handles, each with its own calibration,
+ * matrix, integrator and predictor history) side by side on one device.  A job
+ * is one handle plus a run of frames.  Jobs are admitted into slots while other
+ * jobs are running, as long as a slot is free and the handle's device memory fits
+ * in the server's budget; otherwise rtc_slot_submit returns RTC_EBUSY and the
+ * caller retries once rtc_slot_poll has freed a slot.  Each admitted job gets its
+ * own stream and a fixed share of the SMs (num_SMs / max_slots blocks per frame
+ * kernel), so the work of different jobs overlaps on the device, and a job's
+ * results do not depend on which other jobs run beside it. */
+
+typedef struct rtc_server rtc_server;
+
+/* Errors: RTC_EINVAL (max_slots < 1 or > 32, budget <= 0, device), RTC_ENOMEM. */
+int rtc_server_create(int32_t device, int32_t max_slots, int64_t mem_budget_bytes, rtc_server** out);
+
+/* Wait for running jobs, then release the server (not the handles). */
+int rtc_server_destroy(rtc_server* s);
+
+/* Admit a job: frames host uint16 [n_frames][n_wfs][H][W] (pinned memory keeps the
+ * submission asynchronous), dm_out host float32 [n_frames][nact] receives each
+ * frame's DM commands.  Both stay owned by the caller and must stay valid until
+ * rtc_slot_poll reports the job done; the handle must not be used meanwhile.
+ * *slot receives the slot id.  Errors: RTC_EINVAL, RTC_ESTATE (handle not ready
+ * or already in a slot, or on another device), RTC_EBUSY (no slot or not enough
+ * memory budget now), RTC_EDEVICE. */
+int rtc_slot_submit(rtc_server* s, rtc_handle* h, const uint16_t* frames, uint64_t n_frames,
+                    float* dm_out, int32_t* slot);
+
+/* RTC_OK when the job in `slot` is complete (its results are in dm_out and the slot
+ * and its memory budget are free again), RTC_EBUSY while it runs.  frames_done (may
+ * be NULL) receives the frames completed so far.  Errors: RTC_EINVAL,
+ * RTC_ETIMEDOUT or RTC_EDEVICE (the job failed; the slot is freed). */
+int rtc_slot_poll(rtc_server* s, int32_t slot, uint64_t* frames_done);
+
+/* Jobs running and device bytes they account for. */
+int rtc_server_info(const rtc_server* s, int32_t* active_slots, int64_t* mem_in_use);
+
 /* ---- learned slope predictor --------------------------------------------------
  * An addition to the paper's pipeline: a shared MLP predicts each subaperture's
  * next slopes from its 5x5 neighbourhood over the last 4 frames, to offset the

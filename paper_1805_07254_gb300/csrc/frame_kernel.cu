@@ -10,9 +10,10 @@
 // DARC's horizontal processing overlaps work with pixel arrival (Sec. 2.2).
 //
 // The grid barrier counts block arrivals on a 64-bit counter that only grows;
-// launch number e waits for G * e arrivals, so the counter never needs a reset
-// between launches.  All blocks are co-resident (cooperative launch, one block
-// per SM).
+// each launch waits for the running total of arrivals expected up to and
+// including its own blocks, so the counter never needs a reset between launches
+// (even when the block count changes).  All blocks are co-resident (cooperative
+// launch, one block per SM).
 
 #include "pixel.cuh"
 #include "stream_mvm.cuh"
@@ -75,10 +76,12 @@ cudaError_t launch_dt(rtc_handle* h, const uint16_t* d_frame, float* d_dm_out, c
     if (!L.ok) return cudaErrorInvalidValue;
     const rtc_pixel::PixelArgs px = pixel_args(h, d_frame, h->d_s);
     const Args g = make_args(h, h->d_s, d_dm_out, L.nst, Epc<DT>::v);
-    const unsigned long long target = static_cast<unsigned long long>(L.G) * (h->grid_epoch + 1);
+    // the block count may change between launches (e.g. a server slot limits it), so
+    // the target is the running total of expected arrivals, not launches x blocks
+    const unsigned long long target = h->grid_epoch + static_cast<unsigned long long>(L.G);
     const cudaError_t e = L.s_in_smem ? launch_npx<DT, true>(h, L, px, g, target, st)
                                       : launch_npx<DT, false>(h, L, px, g, target, st);
-    if (e == cudaSuccess) h->grid_epoch += 1;
+    if (e == cudaSuccess) h->grid_epoch = target;
     return e;
 }
 

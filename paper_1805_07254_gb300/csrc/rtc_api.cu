@@ -502,6 +502,27 @@ int rtc_process_frame(rtc_handle* h, const uint16_t* frame, float* dm_out, float
     return take_status(h, h->stream);
 }
 
+}  // extern "C"
+
+int rtc_enqueue_frame(rtc_handle* h, const uint16_t* d_frame, float* d_dm_out, cudaStream_t st) {
+    return enqueue_step(h, d_frame, d_dm_out, nullptr, st);
+}
+
+bool rtc_handle_ready(const rtc_handle* h) { return h && h->calib_loaded && h->store >= 0; }
+
+int64_t rtc_handle_device_bytes(const rtc_handle* h) {
+    const int64_t nact = h->cfg.nact, kpad = h->kpad, nw = h->cfg.n_wfs;
+    const int64_t npp = static_cast<int64_t>(h->cfg.npx) * h->cfg.npx;
+    int64_t b = nact * kpad * std::max(dtype_size(h->store), 1) + 4 * nact;   // matrix + scales
+    b += 2 * 4 * nw * h->n_valid * npp;                                        // dark + gain
+    b += nw * static_cast<int64_t>(h->side) * h->side * 2;                     // frame staging
+    b += 4 * (kpad + nact) + 4 * static_cast<int64_t>(kMaxKsplit) * nact + 4 * nact;  // s, a, partials
+    if (h->pred) b += 4 * (5 * kpad) + 4 * 25 * h->n_valid + 3 * 4 * RTC_MLP_NPARAMS + 2 * (64 * 208 + 64 * 64);
+    return b;
+}
+
+extern "C" {
+
 int rtc_process_frame_async(rtc_handle* h, const uint16_t* d_frame, float* d_dm_out,
                             float* d_slopes_out, void* stream) {
     int rc = check_ready(h);

@@ -67,7 +67,7 @@ struct rtc_handle {
     uint16_t* d_frame = nullptr;    // [n_wfs][side][side] staging for host frames
     int* d_status = nullptr;        // device-side error word (RTC_ETIMEDOUT from bounded waits)
     unsigned long long* d_gridbar = nullptr;  // grid-barrier arrival counter (only grows)
-    unsigned long long grid_epoch = 0;        // fused launches issued against d_gridbar
+    unsigned long long grid_epoch = 0;        // block arrivals expected so far on d_gridbar
 
     // persistent loop (allocated by the first rtc_run_loop)
     float* d_sbuf = nullptr;                  // [2][kpad] slope vectors by frame parity
@@ -78,6 +78,8 @@ struct rtc_handle {
     float* h_dm_ring = nullptr;               // pinned mapped [RTC_LOOP_SLOTS][nact]
     rtc_loop_done* h_done = nullptr;          // pinned mapped [RTC_LOOP_SLOTS]
     int sbuf_kpad = -1;                       // kpad d_sbuf was sized for
+
+    bool in_slot = false;                     // owned by a server slot (rtc_slot_submit)
 
     // learned slope predictor (rtc_load_predictor)
     struct MlpDev* pred = nullptr;            // network weights on the device
@@ -128,6 +130,13 @@ cudaError_t launch_quantise(int store, const float* d_src, int nact, int K, int 
 // Read and clear the device status word after `st` drains (RTC_OK or the recorded
 // error, which also restarts the grid-barrier count); set the handle's message.
 int take_status(rtc_handle* h, cudaStream_t st);
+
+// One frame through the whole path on device buffers, enqueued on st (the work of
+// rtc_process_frame_async after its checks); and whether the handle is ready for it.
+int rtc_enqueue_frame(rtc_handle* h, const uint16_t* d_frame, float* d_dm_out, cudaStream_t st);
+bool rtc_handle_ready(const rtc_handle* h);
+// Device memory the handle holds (matrix, calibration, state, staging).
+int64_t rtc_handle_device_bytes(const rtc_handle* h);
 int fail_handle(rtc_handle* h, int code, const char* msg);
 
 // Message returned by rtc_last_error(NULL) for failures of calls without a handle.

@@ -76,6 +76,11 @@ SIGNATURES = {
     "rtc_mvm_integrate_noalloc": (_I, [_P, C.c_int32, _P, C.c_int32, C.c_int32, _P, _P, _P,
                                        C.c_float, C.c_float, C.c_int32, _P]),
     "rtc_run_loop": (_I, [_P, C.POINTER(RtcLoopConfig), C.POINTER(RtcStats)]),
+    "rtc_server_create": (_I, [C.c_int32, C.c_int32, C.c_int64, C.POINTER(_P)]),
+    "rtc_server_destroy": (_I, [_P]),
+    "rtc_slot_submit": (_I, [_P, _P, _P, C.c_uint64, _P, C.POINTER(C.c_int32)]),
+    "rtc_slot_poll": (_I, [_P, C.c_int32, C.POINTER(C.c_uint64)]),
+    "rtc_server_info": (_I, [_P, C.POINTER(C.c_int32), C.POINTER(C.c_int64)]),
     "rtc_mlp_create": (_I, [C.c_int32, C.POINTER(_P)]),
     "rtc_mlp_destroy": (_I, [_P]),
     "rtc_mlp_set_params": (_I, [_P, _P, C.c_int64]),
@@ -336,6 +341,73 @@ def mvm_integrate_noalloc(d_M, store: str, d_row_scales, nact: int, kpad: int, d
                                        _stream_ptr(stream))
     if rc != RTC_OK:
         raise RtcError(rc, lib.rtc_last_error(None).decode())
+
+
+class Server:
+    """Several controllers served side by side on one GPU (rtc_server_* / rtc_slot_*)."""
+
+    def __init__(self, device: int = 0, max_slots: int = 4, mem_budget: int = 1 << 36):
+        self._lib = load_library()
+        h = _P()
+        rc = self._lib.rtc_server_create(device, max_slots, mem_budget, C.byref(h))
+        if rc != RTC_OK:
+            raise RtcError(rc, self._lib.rtc_last_error(None).decode())
+        self._h = h
+        self._keep = {}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.rtc_server_destroy(self._h)
+            self._h = None
+            self._keep = {}
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def submit(self, rtc: "Rtc", frames) -> int:
+        """Admit a job; returns its slot.  Raises RtcError (code RTC_EBUSY) when no slot
+        or memory budget is free now.  Results: see result(slot)."""
+        import torch
+        fr = torch.from_numpy(np.ascontiguousarray(frames, dtype=np.uint16)).pin_memory()
+        n = fr.shape[0]
+        dm = torch.empty((n, rtc.cfg.nact), dtype=torch.float32).pin_memory()
+        slot = C.c_int32(-1)
+        rc = self._lib.rtc_slot_submit(self._h, rtc.handle, _ptr(fr), n, _ptr(dm), C.byref(slot))
+        if rc != RTC_OK:
+            raise RtcError(rc, self._lib.rtc_last_error(None).decode())
+        self._keep[slot.value] = (fr, dm)
+        return slot.value
+
+    def poll(self, slot: int):
+        """(done, frames_done); raises RtcError if the job failed."""
+        done = C.c_uint64(0)
+        rc = self._lib.rtc_slot_poll(self._h, slot, C.byref(done))
+        if rc == RTC_EBUSY:
+            return False, done.value
+        if rc != RTC_OK:
+            raise RtcError(rc, self._lib.rtc_last_error(None).decode())
+        return True, done.value
+
+    def wait(self, slot: int, timeout_s: float = 120.0) -> np.ndarray:
+        """Block until the job in `slot` is done; returns its DM commands [n_frames][nact]."""
+        import time
+        t0 = time.time()
+        while True:
+            done, _ = self.poll(slot)
+            if done:
+                return self._keep.pop(slot)[1].numpy().copy()
+            if time.time() - t0 > timeout_s:
+                raise TimeoutError(f"slot {slot} not done after {timeout_s} s")
+            time.sleep(0.0005)
+
+    def info(self):
+        a = C.c_int32(0)
+        b = C.c_int64(0)
+        self._lib.rtc_server_info(self._h, C.byref(a), C.byref(b))
+        return {"active_slots": a.value, "mem_in_use": b.value}
 
 
 MLP_NPARAMS = 17154
