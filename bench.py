@@ -47,7 +47,7 @@ def parse_args(argv=None):
     ap.add_argument("--steps", type=int, default=10000)
     ap.add_argument("--warmup", type=int, default=50)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--store", choices=["f32", "bf16", "fp8"], default="f32")
+    ap.add_argument("--store", choices=["f32", "bf16", "f16", "fp8", "int8"], default="f32")
     ap.add_argument("--ksplit", type=int, default=0)
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-loop", action="store_true")
@@ -209,10 +209,10 @@ def run_oracle(cfg, frames, dark, flat, M, budget_s, max_frames):
 
 
 # --------------------------------------------------------------------------- workload
-def make_workload(n_frames, store):
+def make_workload(n_frames, store, cfg=None):
     import numpy as np
     import synth
-    cfg = synth.elt_scao()
+    cfg = cfg or synth.elt_scao()
     frames, _ = synth.make_frames(cfg, 0, n_frames)
     dark, flat = synth.calibration_maps(cfg)
     M = synth.control_matrix(cfg).numpy()
@@ -351,7 +351,7 @@ def ours(args):
 
     variants = {}
     if not args.no_variants:
-        for store in ("f32", "bf16", "fp8"):
+        for store in ("f32", "bf16", "f16", "fp8", "int8"):
             if store == args.store:
                 continue
             rv = controller(store)
@@ -372,12 +372,14 @@ def ours(args):
                                "stage_mvm_hbm_gbs": round(mb / (mv["mean"] * 1e-6) / 1e9, 1)}
             rv.close()
 
-    # reduced precision + learned predictor: BF16 matrix, predictor on (pixel kernel,
-    # predictor kernel, streaming reconstruction); the weights do not change the timing
+    # reduced precision + learned predictor: BF16 matrix, predictor on (pixel stage,
+    # prediction and streaming reconstruction in one launch); the weights do not
+    # change the timing
+    from synth.mlp_init import init_mlp_params, flatten
+    pred_params = flatten(init_mlp_params(0))
     if not args.no_variants:
-        from synth.mlp_init import init_mlp_params, flatten
         rp = controller("bf16")
-        rp.load_predictor(flatten(init_mlp_params(0)), 0.3)
+        rp.load_predictor(pred_params, 0.3)
         rp.set_predictor(True)
         (s3,) = time_steps(torch, rp, d_frames, d_dm, flush, st, min(args.steps, 2000),
                            args.warmup, fused=True)
@@ -385,20 +387,57 @@ def ours(args):
         variants["bf16_predictor"] = {"p50_us": round(sp["p50"], 3), "p99_us": round(sp["p99"], 3),
                                       "p999_us": round(sp["p999"], 3),
                                       "rms_jitter_us": round(sp["rms_jitter"], 3),
-                                      "kernels_per_frame": 3}
+                                      "kernels_per_frame": 1}
         rp.close()
+
+    # stress sizing: six ELT WFS into one 4421 x 47664 FP8 matrix
+    stress = None
+    if not args.no_variants:
+        import synth
+        cfg6, frames6, dark6, flat6, M6 = make_workload(8, "fp8", synth.elt_scao_6wfs())
+        r6 = Rtc(cfg6.nsub, cfg6.npx, cfg6.nact, n_wfs=cfg6.n_wfs, obs=cfg6.obs, gain=cfg6.gain,
+                 leak=cfg6.leak, device=local)
+        r6.load_calib(dark6, flat6)
+        r6.load_cmat(M6, store="fp8")
+        del M6
+        i6 = r6.info()
+        d_frames6 = [torch.from_numpy(frames6[k]).contiguous().to(dev) for k in range(8)]
+        (s6,) = time_steps(torch, r6, d_frames6, d_dm, flush, st, min(args.steps, 2000),
+                           args.warmup, fused=True)
+        q6 = stats_us(s6)
+        b6 = i6["matrix_bytes"] + 4 * i6["nslopes"] + 8 * cfg6.nact + i6["frame_bytes"] + i6["calib_bytes"]
+        st6, _, _ = r6.run_loop(5 * args.loop_frames, rate_hz=0.0, frames=frames6) if not args.no_loop \
+            else ({}, None, None)
+        stress = {"workload": f"6 x {cfg6.frame_side}x{cfg6.frame_side} u16 frames, {cfg6.n_wfs * cfg6.n_valid} "
+                              f"subaps, {cfg6.nact}x{i6['nslopes']} fp8 matrix + row scales",
+                  "p50_us": round(q6["p50"], 3), "p99_us": round(q6["p99"], 3),
+                  "p999_us": round(q6["p999"], 3), "rms_jitter_us": round(q6["rms_jitter"], 3),
+                  "frame_hbm_gbs": round(b6 / (q6["mean"] * 1e-6) / 1e9, 1),
+                  "frame_frac_of_peak": round(b6 / (q6["mean"] * 1e-6) / 1e9 / hbm_peak, 4)}
+        if st6:
+            stress["loop_max"] = {k2: round(st6[k1], 2) for k1, k2 in (
+                ("frames_per_s", "frames_per_s"), ("e2e_p50_us", "e2e_p50_us"), ("e2e_p99_us", "e2e_p99_us"),
+                ("e2e_p999_us", "e2e_p999_us"), ("e2e_rms_jitter_us", "e2e_rms_jitter_us"),
+                ("dev_p50_us", "dev_p50_us"), ("dev_p99_us", "dev_p99_us"))}
+        r6.close()
+        del d_frames6
 
     # persistent real-time loop (rtc_run_loop): frames published by a host thread into
     # pinned mapped memory, DM commands back in host memory; paced at 1 kHz and flat out
     loop = {}
     if not args.no_loop:
-        for store, mode, rate, n in (("f32", "1kHz", 1000.0, args.loop_frames),
-                                     ("f32", "max", 0.0, 5 * args.loop_frames),
-                                     ("bf16", "max", 0.0, 5 * args.loop_frames),
-                                     ("fp8", "max", 0.0, 5 * args.loop_frames)):
+        for store, pred, mode, rate, n in (("f32", False, "1kHz", 1000.0, args.loop_frames),
+                                           ("f32", False, "max", 0.0, 5 * args.loop_frames),
+                                           ("bf16", False, "max", 0.0, 5 * args.loop_frames),
+                                           ("fp8", False, "max", 0.0, 5 * args.loop_frames),
+                                           ("bf16", True, "1kHz", 1000.0, args.loop_frames),
+                                           ("bf16", True, "max", 0.0, 5 * args.loop_frames)):
             rl = controller(store)
+            if pred:
+                rl.load_predictor(pred_params, 0.3)
+                rl.set_predictor(True)
             st_l, _, _ = rl.run_loop(n, rate_hz=rate, frames=frames[:8])
-            loop[f"{store}_{mode}"] = {
+            loop[f"{store}{'_predictor' if pred else ''}_{mode}"] = {
                 "frames": int(st_l["frames"]), "frames_per_s": round(st_l["frames_per_s"], 1),
                 "e2e_p50_us": round(st_l["e2e_p50_us"], 2), "e2e_p99_us": round(st_l["e2e_p99_us"], 2),
                 "e2e_p999_us": round(st_l["e2e_p999_us"], 2),
@@ -449,6 +488,7 @@ def ours(args):
         "clocks": clocks,
         "timed_wall_s_incl_flush": round(t_wall, 3),
         "variants": variants,
+        "stress_6wfs_fp8": stress,
         "loop": loop,
         "cpu_baseline": cpu,
     }

@@ -53,7 +53,9 @@ extern "C" {
 typedef enum rtc_dtype {
     RTC_F32 = 0,        /* IEEE binary32 */
     RTC_BF16 = 1,       /* bfloat16, round-to-nearest-even from FP32 */
-    RTC_FP8_E4M3 = 2    /* E4M3 ("fn": bias 7, max 448) codes with one FP32 scale per row */
+    RTC_FP8_E4M3 = 2,   /* E4M3 ("fn": bias 7, max 448) codes with one FP32 scale per row */
+    RTC_F16 = 3,        /* IEEE binary16, round-to-nearest-even (Sec. 2.3.4's 16-bit format) */
+    RTC_INT8 = 4        /* signed 8-bit codes in [-127, 127] with one FP32 scale per row */
 } rtc_dtype;
 
 typedef struct rtc_config {
@@ -122,13 +124,16 @@ int rtc_load_calib(rtc_handle* h, const float* dark, const float* flat, int64_t 
 int rtc_set_threshold(rtc_handle* h, int32_t mode, float thr);
 
 /* Control matrix for Fig. 3 (c).  M: host, row-major [nact][nslopes] of type
- * src (float32, bf16 bits as uint16, or E4M3 codes as uint8).  nact and nslopes
- * must match the handle.  store selects the device storage: from an RTC_F32
- * source the library quantises on the device (BF16: round to nearest even;
- * FP8: per-row scale = max|M_r| / 448, codes = e4m3_rn_satfinite(M_rj / scale),
- * both divisions in FP32); otherwise store must equal src and, for FP8,
- * row_scales (host float32 [nact]) must be given.  Rows are padded with zeros to
- * kpad entries.  Errors: RTC_EINVAL, RTC_ENOMEM, RTC_EDEVICE. */
+ * src (float32, bf16 or binary16 bits as uint16, E4M3 codes as uint8, or int8
+ * codes).  nact and nslopes must match the handle.  store selects the device
+ * storage: from an RTC_F32 source the library quantises on the device (BF16 and
+ * F16: round to nearest even; FP8: per-row scale = max|M_r| / 448, codes =
+ * e4m3_rn_satfinite(M_rj / scale); INT8: per-row scale = max|M_r| / 127, codes =
+ * clamp(rint(M_rj / scale), -127, 127); every division one FP32 operation; a zero
+ * row gets scale 1); otherwise store must equal src and, for FP8 and INT8,
+ * row_scales (host float32 [nact]) must be given.  The dot product of a scaled
+ * row is scale_r * sum_j code_rj s_j.  Rows are padded with zeros to kpad
+ * entries.  Errors: RTC_EINVAL, RTC_ENOMEM, RTC_EDEVICE. */
 int rtc_load_cmat(rtc_handle* h, const void* M, int32_t nact, int32_t nslopes,
                   int32_t src, int32_t store, const float* row_scales);
 
@@ -153,7 +158,9 @@ int rtc_get_info(const rtc_handle* h, rtc_info* out);
 int rtc_process_frame(rtc_handle* h, const uint16_t* frame, float* dm_out, float* slopes_out);
 
 /* The same step on device buffers, enqueued on `stream` (a cudaStream_t; NULL
- * means the handle's own stream) without synchronising.  d_frame must be 16-byte
+ * means the handle's own non-blocking stream, which does not wait for work on the
+ * legacy default stream: pass cudaStreamLegacy to order the call after such
+ * work) without synchronising.  d_frame must be 16-byte
  * aligned.  d_dm_out (float32 [nact]) and d_slopes_out (float32 [nslopes]) may
  * be NULL.  The integrator state lives on the device; consecutive calls on one
  * stream form the closed loop.  Errors: RTC_EINVAL, RTC_ESTATE, RTC_EDEVICE. */
@@ -334,10 +341,13 @@ int rtc_mlp_train_seq(rtc_mlp* m, const float* d_S, int32_t n_frames, const int3
 int rtc_mlp_predict_seq(rtc_mlp* m, const float* d_S, int32_t n_frames, float sigma, float* d_out,
                         void* stream);
 
-/* Use a predictor in the per-frame path of a handle (SCAO only, n_wfs == 1):
- * params host float32 [RTC_MLP_NPARAMS], sigma the slope scale of the features.
- * The handle keeps the last 4 measured slope vectors; with the predictor on, the
- * reconstruction uses the predicted next slopes instead of the measured ones.
+/* Use a predictor in the per-frame path of a handle (SCAO only, n_wfs == 1, up to
+ * 16384 slopes): params host float32 [RTC_MLP_NPARAMS], sigma the slope scale of
+ * the features.  The handle keeps the last 4 measured slope vectors; with the
+ * predictor on, the reconstruction uses the predicted next slopes
+ * s_k + sigma * y instead of the measured ones, in rtc_process_frame(_async) and
+ * in rtc_run_loop alike (the prediction runs inside the same kernel launch as the
+ * rest of the frame), and slopes_out still receives the measured slopes.
  * rtc_reset clears the history.  Errors: RTC_EINVAL, RTC_ENOMEM, RTC_EDEVICE. */
 int rtc_load_predictor(rtc_handle* h, const float* params, int64_t n, float sigma);
 int rtc_set_predictor(rtc_handle* h, int32_t on);
@@ -359,7 +369,7 @@ int rtc_set_predictor(rtc_handle* h, int32_t on);
  * Buffers (all device memory on the current device, owned by the caller):
  *   d_M          [nact][kpad] matrix in the stored type `store` (rtc_dtype),
  *                rows zero-padded, 16-byte aligned; kpad a multiple of 16;
- *   d_row_scales [nact] FP32 row scales (FP8 only, else may be NULL);
+ *   d_row_scales [nact] FP32 row scales (FP8 and INT8, else may be NULL);
  *   d_s          [kpad] FP32 slopes, zero-padded, 16-byte aligned;
  *   d_a          [nact] FP32 integrator state, updated in place:
  *                a <- leak * a + gain * (M s);

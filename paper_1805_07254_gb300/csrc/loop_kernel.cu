@@ -7,11 +7,19 @@
 //   1. thread 0 of each block spins (bounded, 2 s) on the frame's sequence flag
 //      in pinned host memory (a system-scope acquire load); a stop value ends
 //      the loop;
-//   2. the consumer warps compute the block's share of the slopes, reading the
-//      pixels straight from the host ring with loads that bypass the caches (the
-//      slot is rewritten between its uses);
+//   2. the consumer warps copy the block's share of the frame from the host ring
+//      into a device staging buffer with the widest loads the layout allows
+//      (16 bytes for ELT frames), bypassing the caches (the slot is rewritten
+//      between its uses); a bounded grid barrier makes the whole frame visible,
+//      and the consumers compute the block's share of the slopes from it through
+//      L2 (one coalesced pass over the host link instead of a few scattered
+//      bytes per pixel row);
 //   3. a bounded grid barrier makes the slope vector (double-buffered by frame
 //      parity) visible to all blocks;
+//   3b. with the learned predictor on (PRED), the measured slopes go to the next
+//      row of the handle's history ring instead, the blocks predict the next
+//      slopes of their subapertures (pred_tile.cuh), and a second grid barrier
+//      makes the prediction visible;
 //   4. the streaming reconstruction + integrator; DM commands go to the device
 //      state and to the frame's slot in mapped host memory;
 //   5. the last block to finish publishes the completion record (sequence,
@@ -21,6 +29,7 @@
 // while a frame is being finished.
 
 #include "pixel.cuh"
+#include "pred_tile.cuh"
 #include "stream_mvm.cuh"
 
 namespace {
@@ -35,6 +44,8 @@ struct LoopArgs {
     Args mv;                           // s and dm_out are set per frame
     const uint16_t* frames;            // mapped host ring [nslot][frame_elems]
     unsigned long long frame_elems;
+    uint16_t* stage;                   // device [frame_elems]: this frame's pixels
+    int copy_unit;                     // bytes per copy load: 16, 4 or 2
     const unsigned long long* seq;     // mapped host [nslot]: frame k published as k + 1
     float* dm_ring;                    // mapped host [nslot][nact]
     rtc_loop_done* done;               // mapped host [nslot]
@@ -45,6 +56,8 @@ struct LoopArgs {
     unsigned long long n_frames;
     int nslot;
     int kpad;
+    rtc_pred::PredArgs pa;             // PRED only
+    int head0;                         // PRED: ring row of the newest vector at launch
 };
 
 __device__ __forceinline__ unsigned long long ld_acquire_sys(const unsigned long long* p) {
@@ -56,16 +69,21 @@ __device__ __forceinline__ void st_release_sys(unsigned long long* p, unsigned l
     asm volatile("st.release.sys.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
-template <int DT, bool S_SMEM, int NPX>
+template <int DT, bool S_SMEM, int NPX, bool PRED>
 __global__ void __launch_bounds__(kThreads, 1) loop_kernel(LoopArgs L) {
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ Shared sh;
     __shared__ int stop_now;
     const int tid = threadIdx.x;
     const unsigned long long G = gridDim.x;
-    if (tid == 0) init_shared(sh);
+    // the block's plan lives in shared memory: kept in registers across the frame
+    // loop it would push the reconstruction's working set into local memory
+    __shared__ Plan pl;
+    if (tid == 0) {
+        init_shared(sh);
+        pl = make_plan<DT, S_SMEM>(L.mv, smem);
+    }
     __syncthreads();
-    const Plan pl = make_plan<DT, S_SMEM>(L.mv, smem);
 
     if (tid >= kConsumers) {
         // producers: the matrix does not depend on the frame
@@ -82,6 +100,11 @@ __global__ void __launch_bounds__(kThreads, 1) loop_kernel(LoopArgs L) {
     const int i0 = static_cast<int>(static_cast<long long>(nt) * blockIdx.x / gridDim.x);
     const int i1 = static_cast<int>(static_cast<long long>(nt) * (blockIdx.x + 1) / gridDim.x);
     const int slot_lane = 2 * (tid >> 5) + ((tid >> 4) & 1);
+    constexpr unsigned long long kBarriers = PRED ? 3 : 2;     // grid barriers per frame
+    // the block's share of the frame's copy units
+    const long long n_units = static_cast<long long>(L.frame_elems * 2 / L.copy_unit);
+    const long long u0 = n_units * blockIdx.x / gridDim.x;
+    const long long u1 = n_units * (blockIdx.x + 1) / gridDim.x;
     int tile = 0;
     for (unsigned long long k = 0; k < L.n_frames; ++k) {
         const int slot = static_cast<int>(k % L.nslot);
@@ -109,24 +132,54 @@ __global__ void __launch_bounds__(kThreads, 1) loop_kernel(LoopArgs L) {
         consumer_sync();
         if (stop_now) break;
 
-        // 2. this block's share of the slopes, pixels read from the host ring
+        // 2. the block's share of the frame into device memory, then the block's
+        //    share of the slopes from it
         const uint16_t* frame = L.frames + static_cast<size_t>(slot) * L.frame_elems;
-        float* s_k = L.s_buf + static_cast<size_t>(k & 1) * L.kpad;
+        if (L.copy_unit == 16) {
+            const uint4* src = reinterpret_cast<const uint4*>(frame);
+            uint4* dst = reinterpret_cast<uint4*>(L.stage);
+            for (long long c = u0 + tid; c < u1; c += kConsumers) __stcg(dst + c, __ldcv(src + c));
+        } else if (L.copy_unit == 4) {
+            const unsigned* src = reinterpret_cast<const unsigned*>(frame);
+            unsigned* dst = reinterpret_cast<unsigned*>(L.stage);
+            for (long long c = u0 + tid; c < u1; c += kConsumers) __stcg(dst + c, __ldcv(src + c));
+        } else {
+            for (long long c = u0 + tid; c < u1; c += kConsumers)
+                __stcg(reinterpret_cast<unsigned short*>(L.stage) + c,
+                       __ldcv(reinterpret_cast<const unsigned short*>(frame) + c));
+        }
+        consumer_sync();
+        if (tid == 0) grid_barrier(L.gridbar, G * (kBarriers * k + 1), L.mv.status, &sh.abort_flag);
+        consumer_sync();
+        if (sh.abort_flag) break;
+        const int head = (L.head0 + 1 + static_cast<int>(k & 3)) & 3;
+        float* s_k = PRED ? L.pa.ring + static_cast<size_t>(head) * L.kpad
+                          : L.s_buf + static_cast<size_t>(k & 1) * L.kpad;
         for (int base = i0; base < i1; base += 2 * kConsumerWarps) {
             const int gi = base + slot_lane;
-            rtc_pixel::subap_slopes<NPX, rtc_pixel::kPixelVolatile, 16>(L.px, frame, s_k, gi, gi < i1,
-                                                                        tid & 31);
+            rtc_pixel::subap_slopes<NPX, rtc_pixel::kPixelL2, 16>(L.px, L.stage, s_k, gi, gi < i1,
+                                                                  tid & 31);
         }
 
         // 3. the whole slope vector visible to every block
         consumer_sync();
-        if (tid == 0) grid_barrier(L.gridbar, G * (k + 1), L.mv.status, &sh.abort_flag);
+        if (tid == 0) grid_barrier(L.gridbar, G * (kBarriers * k + 2), L.mv.status, &sh.abort_flag);
         consumer_sync();
         if (sh.abort_flag) break;
 
+        // 3b. predicted next slopes
+        const float* s_vec = s_k;
+        if (PRED) {
+            rtc_pred::predict(L.pa, pl.scratch, tid, i0, i1, head);
+            if (tid == 0) grid_barrier(L.gridbar, G * (kBarriers * k + 3), L.mv.status, &sh.abort_flag);
+            consumer_sync();
+            if (sh.abort_flag) break;
+            s_vec = L.pa.s_pred;
+        }
+
         // 4. reconstruction and integrator
-        consumer_prologue<DT, S_SMEM, true>(L.mv, pl, tid, s_k);
-        tile = consume<DT, S_SMEM, true>(L.mv, pl, sh, tid, tile, s_k,
+        consumer_prologue<DT, S_SMEM, true>(L.mv, pl, tid, s_vec);
+        tile = consume<DT, S_SMEM, true>(L.mv, pl, sh, tid, tile, s_vec,
                                          L.dm_ring + static_cast<size_t>(slot) * L.mv.nact);
 
         // 5. the last block to finish publishes the completion record
@@ -145,22 +198,27 @@ __global__ void __launch_bounds__(kThreads, 1) loop_kernel(LoopArgs L) {
     }
 }
 
-template <int DT, bool S, int NPX>
+template <int DT, bool S, int NPX, bool PRED>
 cudaError_t launch_t(const Launch& Lc, LoopArgs a, cudaStream_t st) {
     void* args[] = {&a};
-    return cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(loop_kernel<DT, S, NPX>),
+    return cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(loop_kernel<DT, S, NPX, PRED>),
                                        dim3(Lc.G), dim3(kThreads), args, Lc.smem, st);
 }
 
 template <int DT>
 cudaError_t launch_dt(rtc_handle* h, const LoopLaunch& ll, cudaStream_t st) {
-    const Launch Lc = plan_launch(h, Epc<DT>::v);
-    if (!Lc.ok) return cudaErrorInvalidValue;
-    LoopArgs a;
+    const bool pred = h->pred_on;
+    const Launch Lc = plan_launch(h, Epc<DT>::v, pred ? rtc_pred::kSmemBytes : 0);
+    if (!Lc.ok || (pred && !Lc.s_in_smem)) return cudaErrorInvalidValue;
+    LoopArgs a{};
     a.px = pixel_args(h, nullptr, nullptr);
-    a.mv = make_args(h, nullptr, nullptr, Lc.nst, Epc<DT>::v);
+    a.mv = make_args(h, nullptr, nullptr, Lc, Epc<DT>::v);
     a.frames = ll.d_frames;
     a.frame_elems = ll.frame_elems;
+    a.stage = h->d_frame;
+    const size_t fbytes = ll.frame_elems * 2;
+    const uintptr_t bases = reinterpret_cast<uintptr_t>(ll.d_frames) | reinterpret_cast<uintptr_t>(h->d_frame);
+    a.copy_unit = (fbytes % 16 == 0 && bases % 16 == 0) ? 16 : (fbytes % 4 == 0 && bases % 4 == 0) ? 4 : 2;
     a.seq = ll.d_seq;
     a.dm_ring = ll.d_dm;
     a.done = ll.d_done;
@@ -172,23 +230,30 @@ cudaError_t launch_dt(rtc_handle* h, const LoopLaunch& ll, cudaStream_t st) {
     a.nslot = ll.nslot;
     a.kpad = h->kpad;
     const bool npx10 = h->cfg.npx == 10;
+    if (pred) {
+        a.pa = pred_args(h);
+        a.head0 = h->ring_head;
+        return npx10 ? launch_t<DT, true, 10, true>(Lc, a, st) : launch_t<DT, true, 0, true>(Lc, a, st);
+    }
     if (Lc.s_in_smem)
-        return npx10 ? launch_t<DT, true, 10>(Lc, a, st) : launch_t<DT, true, 0>(Lc, a, st);
-    return npx10 ? launch_t<DT, false, 10>(Lc, a, st) : launch_t<DT, false, 0>(Lc, a, st);
+        return npx10 ? launch_t<DT, true, 10, false>(Lc, a, st) : launch_t<DT, true, 0, false>(Lc, a, st);
+    return npx10 ? launch_t<DT, false, 10, false>(Lc, a, st) : launch_t<DT, false, 0, false>(Lc, a, st);
 }
 
-template <int DT, bool S, int NPX>
+template <int DT, bool S, int NPX, bool PRED>
 cudaError_t configure_t() {
-    return cudaFuncSetAttribute(loop_kernel<DT, S, NPX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    return cudaFuncSetAttribute(loop_kernel<DT, S, NPX, PRED>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 static_cast<int>(kDynSmemBudget));
 }
 
 template <int DT>
 cudaError_t configure_dt() {
-    cudaError_t e = configure_t<DT, true, 10>();
-    if (e == cudaSuccess) e = configure_t<DT, true, 0>();
-    if (e == cudaSuccess) e = configure_t<DT, false, 10>();
-    if (e == cudaSuccess) e = configure_t<DT, false, 0>();
+    cudaError_t e = configure_t<DT, true, 10, false>();
+    if (e == cudaSuccess) e = configure_t<DT, true, 0, false>();
+    if (e == cudaSuccess) e = configure_t<DT, false, 10, false>();
+    if (e == cudaSuccess) e = configure_t<DT, false, 0, false>();
+    if (e == cudaSuccess) e = configure_t<DT, true, 10, true>();
+    if (e == cudaSuccess) e = configure_t<DT, true, 0, true>();
     return e;
 }
 
@@ -197,7 +262,9 @@ cudaError_t configure_dt() {
 cudaError_t loop_kernel_configure() {
     cudaError_t e = configure_dt<RTC_F32>();
     if (e == cudaSuccess) e = configure_dt<RTC_BF16>();
+    if (e == cudaSuccess) e = configure_dt<RTC_F16>();
     if (e == cudaSuccess) e = configure_dt<RTC_FP8_E4M3>();
+    if (e == cudaSuccess) e = configure_dt<RTC_INT8>();
     return e;
 }
 
@@ -205,7 +272,9 @@ cudaError_t launch_loop(rtc_handle* h, const LoopLaunch& ll, cudaStream_t st) {
     switch (h->store) {
         case RTC_F32: return launch_dt<RTC_F32>(h, ll, st);
         case RTC_BF16: return launch_dt<RTC_BF16>(h, ll, st);
+        case RTC_F16: return launch_dt<RTC_F16>(h, ll, st);
         case RTC_FP8_E4M3: return launch_dt<RTC_FP8_E4M3>(h, ll, st);
+        case RTC_INT8: return launch_dt<RTC_INT8>(h, ll, st);
         default: return cudaErrorInvalidValue;
     }
 }

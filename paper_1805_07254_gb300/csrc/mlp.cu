@@ -23,6 +23,7 @@
 
 #include "rtc_internal.h"
 #include "mlp.h"
+#include "pred_tile.cuh"
 
 namespace {
 
@@ -82,7 +83,7 @@ __device__ __forceinline__ void warp_gemm(const bf16* A, int lda, int m0, const 
     }
 }
 
-__device__ __forceinline__ float gelu(float z) { return 0.5f * z * (1.f + erff(z * 0.70710678118654752f)); }
+using rtc_pred::gelu;     // the same function as the fused inference
 __device__ __forceinline__ float gelu_grad(float z) {
     return 0.5f * (1.f + erff(z * 0.70710678118654752f)) + z * 0.39894228040143268f * expf(-0.5f * z * z);
 }
@@ -226,7 +227,6 @@ __device__ void backward_tile(unsigned char* sm, int ns, float inv_batch, float*
     bf16* DZ2 = reinterpret_cast<bf16*>(sm + Smem::DZ2);
     bf16* DZ2T = reinterpret_cast<bf16*>(sm + Smem::DZ2T);
     bf16* DZ1T = reinterpret_cast<bf16*>(sm + Smem::DZ1T);
-    float* RED = reinterpret_cast<float*>(sm + Smem::RED);
     float* LOSS = reinterpret_cast<float*>(sm + Smem::LOSS);
 
     // dy = (y - t) / B for real samples, 0 for padding rows; loss partial sum
@@ -447,7 +447,7 @@ __global__ void __launch_bounds__(kThreads) mlp_predict_kernel(MlpDev w, const f
     for (int q = threadIdx.x; q < ns * NO; q += kThreads) {
         const int s = q / NO, o = q - s * NO;
         const int idx = o * nv + s0 + s;
-        s_pred[idx] = hf.rows[0][idx] + sigma * Y[q];
+        s_pred[idx] = __fmaf_rn(sigma, Y[q], hf.rows[0][idx]);
     }
 }
 

@@ -7,9 +7,9 @@
 //     thread t takes the 16-byte chunks t, t+256, ... of the slice for all four
 //     rows, so each s chunk (read through L1) serves four matrix chunks, and the
 //     matrix is read with L1-bypassing non-coherent 16-byte loads;
-//   - stored values are widened to FP32 just before the FMA (BF16 by a shift,
-//     E4M3 by the hardware fp8x2 -> f16x2 conversion), as Sec. 2.3.4 widens
-//     its 16-bit matrix; the FP8 row scale is applied once, after the sum;
+//   - stored values are widened to FP32 just before the FMA (the widening dot
+//     products of stream_mvm.cuh), as Sec. 2.3.4 widens its 16-bit matrix; the
+//     FP8 and INT8 row scales are applied once, after the sum;
 //   - partials are combined in a fixed order: xor butterfly within the warp,
 //     a pairwise tree over the 8 warps, and, when K is split across blocks, a
 //     pairwise tree over the ksplit block partials done by the last block to
@@ -22,6 +22,7 @@
 #include <cuda_fp8.h>
 
 #include "rtc_internal.h"
+#include "stream_mvm.cuh"
 
 namespace {
 
@@ -33,60 +34,9 @@ __device__ __forceinline__ uint4 ld_stream(const uint4* p) {
     return v;
 }
 
-// Elements of the stored type per 16-byte chunk.
-template <int DT> struct Epc;
-template <> struct Epc<RTC_F32> { static constexpr int v = 4; };
-template <> struct Epc<RTC_BF16> { static constexpr int v = 8; };
-template <> struct Epc<RTC_FP8_E4M3> { static constexpr int v = 16; };
-
-__device__ __forceinline__ float bf16_lo(uint32_t u) { return __uint_as_float(u << 16); }
-__device__ __forceinline__ float bf16_hi(uint32_t u) { return __uint_as_float(u & 0xffff0000u); }
-
-__device__ __forceinline__ float2 e4m3x2_to_float2(uint32_t two_codes) {
-    __half2_raw hr = __nv_cvt_fp8x2_to_halfraw2(static_cast<__nv_fp8x2_storage_t>(two_codes),
-                                                __NV_E4M3);
-    return __half22float2(*reinterpret_cast<__half2*>(&hr));
-}
-
-// acc += <chunk m, s values sv[0 .. Epc)>
-template <int DT>
-__device__ __forceinline__ float chunk_dot(float acc, const uint4& m, const float* sv);
-
-template <>
-__device__ __forceinline__ float chunk_dot<RTC_F32>(float acc, const uint4& m, const float* sv) {
-    acc = fmaf(__uint_as_float(m.x), sv[0], acc);
-    acc = fmaf(__uint_as_float(m.y), sv[1], acc);
-    acc = fmaf(__uint_as_float(m.z), sv[2], acc);
-    acc = fmaf(__uint_as_float(m.w), sv[3], acc);
-    return acc;
-}
-
-template <>
-__device__ __forceinline__ float chunk_dot<RTC_BF16>(float acc, const uint4& m, const float* sv) {
-    const uint32_t w[4] = {m.x, m.y, m.z, m.w};
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        acc = fmaf(bf16_lo(w[j]), sv[2 * j], acc);
-        acc = fmaf(bf16_hi(w[j]), sv[2 * j + 1], acc);
-    }
-    return acc;
-}
-
-template <>
-__device__ __forceinline__ float chunk_dot<RTC_FP8_E4M3>(float acc, const uint4& m,
-                                                         const float* sv) {
-    const uint32_t w[4] = {m.x, m.y, m.z, m.w};
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        const float2 a = e4m3x2_to_float2(w[j] & 0xffffu);
-        const float2 b = e4m3x2_to_float2(w[j] >> 16);
-        acc = fmaf(a.x, sv[4 * j + 0], acc);
-        acc = fmaf(a.y, sv[4 * j + 1], acc);
-        acc = fmaf(b.x, sv[4 * j + 2], acc);
-        acc = fmaf(b.y, sv[4 * j + 3], acc);
-    }
-    return acc;
-}
+using rtc_mvm::chunk_dot;
+using rtc_mvm::Epc;
+using rtc_mvm::RowScaled;
 
 template <int DT>
 __device__ __forceinline__ void load_s(const float* __restrict__ s, int chunk, float* sv) {
@@ -202,7 +152,7 @@ mvm_splitk_kernel(const uint4* __restrict__ M, int chunks_per_row, int nact,
 
     if (t < R && row0 + t < nact) {
         const int row = row0 + t;
-        if (DT == RTC_FP8_E4M3) d *= row_scale[row];
+        if (RowScaled<DT>::v) d *= row_scale[row];
         const float an = fmaf(leak, a[row], gain * d);
         a[row] = an;
         if (dm_out) dm_out[row] = an;
@@ -220,8 +170,28 @@ __global__ void pad_bf16_kernel(const float* __restrict__ src, int K, int kpad,
     }
 }
 
-__global__ void quant_fp8_kernel(const float* __restrict__ src, int K, int kpad,
-                                 __nv_fp8_storage_t* __restrict__ dst, float* __restrict__ scale) {
+__global__ void pad_f16_kernel(const float* __restrict__ src, int K, int kpad, __half* __restrict__ dst) {
+    const int row = blockIdx.x;
+    for (int j = threadIdx.x; j < kpad; j += blockDim.x) {
+        const float v = j < K ? src[static_cast<size_t>(row) * K + j] : 0.f;
+        dst[static_cast<size_t>(row) * kpad + j] = __float2half_rn(v);
+    }
+}
+
+// Code of x / sc in the row-scaled formats (one correctly rounded FP32 division).
+template <int DT>
+__device__ __forceinline__ unsigned char encode_scaled(float x, float sc) {
+    const float q = __fdiv_rn(x, sc);
+    if (DT == RTC_FP8_E4M3) return __nv_cvt_float_to_fp8(q, __NV_SATFINITE, __NV_E4M3);
+    const int i = max(-127, min(127, __float2int_rn(q)));       // nearest, ties to even
+    return static_cast<unsigned char>(static_cast<signed char>(i));
+}
+
+// Per-row scale = max |M_r| / qmax (1 for a zero row) and the row's codes.
+template <int DT>
+__global__ void quant_rowscaled_kernel(const float* __restrict__ src, int K, int kpad,
+                                       unsigned char* __restrict__ dst, float* __restrict__ scale) {
+    constexpr float qmax = DT == RTC_FP8_E4M3 ? 448.0f : 127.0f;
     __shared__ float wmax[32];
     __shared__ float row_scale;
     const int row = blockIdx.x;
@@ -234,16 +204,21 @@ __global__ void quant_fp8_kernel(const float* __restrict__ src, int K, int kpad,
     if (threadIdx.x == 0) {
         float mm = 0.f;
         for (int w = 0; w < static_cast<int>(blockDim.x >> 5); ++w) mm = fmaxf(mm, wmax[w]);
-        row_scale = mm > 0.f ? __fdiv_rn(mm, 448.0f) : 1.0f;
+        row_scale = mm > 0.f ? __fdiv_rn(mm, qmax) : 1.0f;
         scale[row] = row_scale;
     }
     __syncthreads();
     const float sc = row_scale;
-    for (int j = threadIdx.x; j < kpad; j += blockDim.x) {
-        __nv_fp8_storage_t q = 0;
-        if (j < K) q = __nv_cvt_float_to_fp8(__fdiv_rn(in[j], sc), __NV_SATFINITE, __NV_E4M3);
-        dst[static_cast<size_t>(row) * kpad + j] = q;
-    }
+    for (int j = threadIdx.x; j < kpad; j += blockDim.x)
+        dst[static_cast<size_t>(row) * kpad + j] = j < K ? encode_scaled<DT>(in[j], sc) : 0;
+}
+
+template <int DT>
+void launch_raw_t(dim3 grid, const uint4* M, int kpad, int nact, const float* d_s, const float* d_scale,
+                  int ksplit, float* d_partial, unsigned* d_count, float* d_a, float* d_dm_out,
+                  float gain, float leak, cudaStream_t st) {
+    mvm_splitk_kernel<DT, 2><<<grid, kMvmThreads, 0, st>>>(M, kpad / Epc<DT>::v, nact, d_s, d_scale, ksplit,
+                                                           d_partial, d_count, d_a, d_dm_out, gain, leak);
 }
 
 }  // namespace
@@ -255,19 +230,19 @@ cudaError_t launch_mvm_raw(int store, const void* d_M, const float* d_scale, int
     const uint4* M = static_cast<const uint4*>(d_M);
     switch (store) {
         case RTC_F32:
-            mvm_splitk_kernel<RTC_F32, 2><<<grid, kMvmThreads, 0, st>>>(
-                M, kpad / Epc<RTC_F32>::v, nact, d_s, d_scale, ksplit, d_partial, d_count, d_a,
-                d_dm_out, gain, leak);
+            launch_raw_t<RTC_F32>(grid, M, kpad, nact, d_s, d_scale, ksplit, d_partial, d_count, d_a, d_dm_out, gain, leak, st);
             break;
         case RTC_BF16:
-            mvm_splitk_kernel<RTC_BF16, 2><<<grid, kMvmThreads, 0, st>>>(
-                M, kpad / Epc<RTC_BF16>::v, nact, d_s, d_scale, ksplit, d_partial, d_count, d_a,
-                d_dm_out, gain, leak);
+            launch_raw_t<RTC_BF16>(grid, M, kpad, nact, d_s, d_scale, ksplit, d_partial, d_count, d_a, d_dm_out, gain, leak, st);
+            break;
+        case RTC_F16:
+            launch_raw_t<RTC_F16>(grid, M, kpad, nact, d_s, d_scale, ksplit, d_partial, d_count, d_a, d_dm_out, gain, leak, st);
             break;
         case RTC_FP8_E4M3:
-            mvm_splitk_kernel<RTC_FP8_E4M3, 2><<<grid, kMvmThreads, 0, st>>>(
-                M, kpad / Epc<RTC_FP8_E4M3>::v, nact, d_s, d_scale, ksplit, d_partial, d_count,
-                d_a, d_dm_out, gain, leak);
+            launch_raw_t<RTC_FP8_E4M3>(grid, M, kpad, nact, d_s, d_scale, ksplit, d_partial, d_count, d_a, d_dm_out, gain, leak, st);
+            break;
+        case RTC_INT8:
+            launch_raw_t<RTC_INT8>(grid, M, kpad, nact, d_s, d_scale, ksplit, d_partial, d_count, d_a, d_dm_out, gain, leak, st);
             break;
         default:
             return cudaErrorInvalidValue;
@@ -278,13 +253,22 @@ cudaError_t launch_mvm_raw(int store, const void* d_M, const float* d_scale, int
 cudaError_t launch_quantise(int store, const float* d_src, int nact, int K, int kpad, void* d_dst,
                             float* d_scale, cudaStream_t st) {
     if (nact <= 0) return cudaSuccess;
-    if (store == RTC_BF16) {
-        pad_bf16_kernel<<<nact, 256, 0, st>>>(d_src, K, kpad, static_cast<__nv_bfloat16*>(d_dst));
-    } else if (store == RTC_FP8_E4M3) {
-        quant_fp8_kernel<<<nact, 256, 0, st>>>(d_src, K, kpad,
-                                               static_cast<__nv_fp8_storage_t*>(d_dst), d_scale);
-    } else {
-        return cudaErrorInvalidValue;
+    unsigned char* q = static_cast<unsigned char*>(d_dst);
+    switch (store) {
+        case RTC_BF16:
+            pad_bf16_kernel<<<nact, 256, 0, st>>>(d_src, K, kpad, static_cast<__nv_bfloat16*>(d_dst));
+            break;
+        case RTC_F16:
+            pad_f16_kernel<<<nact, 256, 0, st>>>(d_src, K, kpad, static_cast<__half*>(d_dst));
+            break;
+        case RTC_FP8_E4M3:
+            quant_rowscaled_kernel<RTC_FP8_E4M3><<<nact, 256, 0, st>>>(d_src, K, kpad, q, d_scale);
+            break;
+        case RTC_INT8:
+            quant_rowscaled_kernel<RTC_INT8><<<nact, 256, 0, st>>>(d_src, K, kpad, q, d_scale);
+            break;
+        default:
+            return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
 }

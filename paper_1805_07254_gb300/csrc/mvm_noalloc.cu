@@ -50,10 +50,12 @@ extern "C" int rtc_mvm_integrate_noalloc(const void* d_M, int32_t store, const f
     if (ksplit < 1 || ksplit > RTC_NOALLOC_MAX_KSPLIT)
         return noalloc_fail(RTC_EINVAL, "ksplit must be in 1..RTC_NOALLOC_MAX_KSPLIT (16)");
     if (kpad < 0 || kpad % 16 != 0) return noalloc_fail(RTC_EINVAL, "kpad must be a multiple of 16");
-    if (store != RTC_F32 && store != RTC_BF16 && store != RTC_FP8_E4M3)
+    if (store != RTC_F32 && store != RTC_BF16 && store != RTC_F16 && store != RTC_FP8_E4M3 &&
+        store != RTC_INT8)
         return noalloc_fail(RTC_EINVAL, "unknown store type");
     if (!d_s || !d_a || (kpad > 0 && !d_M)) return noalloc_fail(RTC_EINVAL, "NULL buffer");
-    if (store == RTC_FP8_E4M3 && !d_row_scales) return noalloc_fail(RTC_EINVAL, "FP8 needs row scales");
+    if ((store == RTC_FP8_E4M3 || store == RTC_INT8) && !d_row_scales)
+        return noalloc_fail(RTC_EINVAL, "FP8 and INT8 need row scales");
     if ((reinterpret_cast<uintptr_t>(d_M) | reinterpret_cast<uintptr_t>(d_s)) & 15)
         return noalloc_fail(RTC_EINVAL, "d_M and d_s must be 16-byte aligned");
 

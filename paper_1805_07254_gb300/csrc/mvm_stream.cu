@@ -40,7 +40,7 @@ template <int DT>
 cudaError_t launch_stream(const rtc_handle* h, const float* d_s, float* d_dm_out, cudaStream_t st) {
     const Launch L = plan_launch(h, Epc<DT>::v);
     if (!L.ok) return cudaErrorInvalidValue;
-    const Args g = make_args(h, d_s, d_dm_out, L.nst, Epc<DT>::v);
+    const Args g = make_args(h, d_s, d_dm_out, L, Epc<DT>::v);
     if (L.s_in_smem)
         mvm_stream_kernel<DT, true><<<L.G, kThreads, L.smem, st>>>(g);
     else
@@ -61,8 +61,12 @@ cudaError_t mvm_stream_configure() {
     if (e == cudaSuccess) e = configure_one<RTC_F32, false>();
     if (e == cudaSuccess) e = configure_one<RTC_BF16, true>();
     if (e == cudaSuccess) e = configure_one<RTC_BF16, false>();
+    if (e == cudaSuccess) e = configure_one<RTC_F16, true>();
+    if (e == cudaSuccess) e = configure_one<RTC_F16, false>();
     if (e == cudaSuccess) e = configure_one<RTC_FP8_E4M3, true>();
     if (e == cudaSuccess) e = configure_one<RTC_FP8_E4M3, false>();
+    if (e == cudaSuccess) e = configure_one<RTC_INT8, true>();
+    if (e == cudaSuccess) e = configure_one<RTC_INT8, false>();
     return e;
 }
 
@@ -77,7 +81,9 @@ cudaError_t launch_mvm_integrate(const rtc_handle* h, const float* d_s, float* d
     switch (h->store) {
         case RTC_F32: return launch_stream<RTC_F32>(h, d_s, d_dm_out, st);
         case RTC_BF16: return launch_stream<RTC_BF16>(h, d_s, d_dm_out, st);
+        case RTC_F16: return launch_stream<RTC_F16>(h, d_s, d_dm_out, st);
         case RTC_FP8_E4M3: return launch_stream<RTC_FP8_E4M3>(h, d_s, d_dm_out, st);
+        case RTC_INT8: return launch_stream<RTC_INT8>(h, d_s, d_dm_out, st);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -58,15 +58,21 @@ struct PixelArgs {
 };
 
 // How raw pixels are read: through the read-only path (a frame that does not change
-// while the kernel runs), or fetched fresh every time (a frame buffer that a host
-// producer rewrites while a persistent kernel keeps running).
-enum PixelLoad { kPixelReadOnly = 0, kPixelVolatile = 1 };
+// while the kernel runs), fetched fresh every time (a frame buffer that a host
+// producer rewrites while a persistent kernel keeps running), or through L2 (a
+// device buffer that other blocks of the same kernel rewrite frame after frame).
+enum PixelLoad { kPixelReadOnly = 0, kPixelVolatile = 1, kPixelL2 = 2 };
 
 template <int LD>
 __device__ __forceinline__ uint16_t load_pixel(const uint16_t* ptr) {
     if (LD == kPixelVolatile) return __ldcv(ptr);
+    if (LD == kPixelL2) return __ldcg(ptr);
     return __ldg(ptr);
 }
+
+struct NoHook {
+    __device__ void operator()() const {}
+};
 
 // Slopes of subaperture gi (= w * n_valid + i) by an aligned group of L lanes
 // (L = 32: the whole warp; L = 16: each half-warp takes its own subaperture).
@@ -75,15 +81,18 @@ __device__ __forceinline__ uint16_t load_pixel(const uint16_t* ptr) {
 // NPX > 0: box size known at compile time; NPX == 0: p.npx at run time.
 // frame and s_out: this frame's pixels and slope vector (PixelArgs' own fields are
 // not used, so that a persistent kernel can switch buffers per frame cheaply).
-template <int NPX, int LD, int L>
+// loaded(): called by every lane after each pass has issued its loads (the
+// passes are the same for every lane, valid or not).
+template <int NPX, int LD, int L, typename Hook = NoHook>
 __device__ __forceinline__ void subap_slopes(const PixelArgs& p, const uint16_t* __restrict__ frame,
-                                             float* __restrict__ s_out, int gi, bool valid, int lane) {
+                                             float* __restrict__ s_out, int gi, bool valid, int lane,
+                                             const Hook& loaded = Hook()) {
     constexpr int kJ = NPX > 0 ? (NPX * NPX + L - 1) / L : kPixPerLane;
     const int npx = NPX > 0 ? NPX : p.npx;
     const int l = lane & (L - 1);
     const int w = valid ? gi / p.n_valid : 0;
     const int i = valid ? gi - w * p.n_valid : 0;
-    const int npp = valid ? npx * npx : 0;
+    const int npp = npx * npx;
     const int2 pos = valid ? p.rc[i] : make_int2(0, 0);
     const float cc = 0.5f * static_cast<float>(npx - 1);
     const uint16_t* box = frame + static_cast<size_t>(w) * p.side * p.side +
@@ -98,17 +107,19 @@ __device__ __forceinline__ void subap_slopes(const PixelArgs& p, const uint16_t*
 #pragma unroll
         for (int j = 0; j < kJ; ++j) {
             const int q = q0 + l + L * j;
-            if (q < npp) {
+            raw[j] = dv[j] = gv[j] = 0.f;
+            if (valid && q < npp) {
                 const int y = q / npx;
                 raw[j] = static_cast<float>(load_pixel<LD>(box + y * p.side + (q - y * npx)));
                 dv[j] = __ldg(dk + q);
                 gv[j] = __ldg(gk + q);
             }
         }
+        loaded();
 #pragma unroll
         for (int j = 0; j < kJ; ++j) {
             const int q = q0 + l + L * j;
-            if (q < npp) {
+            if (valid && q < npp) {
                 const int y = q / npx;
                 const int x = q - y * npx;
                 float v = __fmul_rn(__fsub_rn(raw[j], dv[j]), gv[j]);

@@ -70,7 +70,9 @@ int dtype_size(int dt) {
     switch (dt) {
         case RTC_F32: return 4;
         case RTC_BF16: return 2;
+        case RTC_F16: return 2;
         case RTC_FP8_E4M3: return 1;
+        case RTC_INT8: return 1;
         default: return 0;
     }
 }
@@ -165,25 +167,24 @@ int check_ready(rtc_handle* h) {
     return RTC_OK;
 }
 
+// s_used (optional) receives the device buffer that holds this frame's measured slopes.
 int enqueue_step(rtc_handle* h, const uint16_t* d_frame, float* d_dm_out, float* d_slopes_out,
-                 cudaStream_t st) {
+                 cudaStream_t st, const float** s_used = nullptr) {
+    if (s_used) *s_used = h->d_s;
     if (h->pred_on && h->kpad > 0) {
-        // measured slopes into the history ring, predicted next slopes, then the
-        // reconstruction from the prediction
+        // measured slopes into the next row of the history ring, the prediction from
+        // the 4 newest rows, the reconstruction from the prediction: one launch
         const int head = (h->ring_head + 1) & 3;
         float* s_meas = h->d_ring + static_cast<size_t>(head) * h->kpad;
-        RTC_CUDA(h, launch_calib_cog(h, d_frame, s_meas, st));
-        RTC_CUDA(h, mlp_launch_predict(*h->pred, h->d_ring, h->kpad, head, h->n_valid, h->d_nbr,
-                                       h->pred_sigma, h->d_spred, st));
-        RTC_CUDA(h, launch_mvm_integrate(h, h->d_spred, d_dm_out, st));
+        RTC_CUDA(h, launch_frame(h, d_frame, d_dm_out, s_meas, head, st));
         h->ring_head = head;
-        RTC_CUDA(h, cudaMemcpyAsync(h->d_s, s_meas, h->kpad * sizeof(float), cudaMemcpyDeviceToDevice, st));
+        if (s_used) *s_used = s_meas;
         if (d_slopes_out)
             RTC_CUDA(h, cudaMemcpyAsync(d_slopes_out, s_meas, h->nslopes * sizeof(float),
                                         cudaMemcpyDeviceToDevice, st));
         return RTC_OK;
     }
-    RTC_CUDA(h, launch_frame(h, d_frame, d_dm_out, st));
+    RTC_CUDA(h, launch_frame(h, d_frame, d_dm_out, nullptr, 0, st));
     if (d_slopes_out)
         RTC_CUDA(h, cudaMemcpyAsync(d_slopes_out, h->d_s, h->nslopes * sizeof(float),
                                     cudaMemcpyDeviceToDevice, st));
@@ -360,7 +361,8 @@ int rtc_load_cmat(rtc_handle* h, const void* M, int32_t nact, int32_t nslopes, i
         return fail(h, RTC_EINVAL, "matrix is %dx%d, handle expects %dx%d", nact, nslopes, h->cfg.nact, h->nslopes);
     if (dtype_size(src) == 0 || dtype_size(store) == 0) return fail(h, RTC_EINVAL, "unknown dtype");
     if (src != RTC_F32 && src != store) return fail(h, RTC_EINVAL, "only an FP32 source can be converted");
-    if (src == RTC_FP8_E4M3 && !row_scales) return fail(h, RTC_EINVAL, "FP8 source needs row_scales");
+    const bool scaled = store == RTC_FP8_E4M3 || store == RTC_INT8;
+    if (src == store && scaled && !row_scales) return fail(h, RTC_EINVAL, "FP8 and INT8 sources need row_scales");
     DeviceScope ds(h->cfg.device);
     RTC_CUDA(h, cudaStreamSynchronize(h->stream));
     free_dev(h->d_M);
@@ -382,7 +384,7 @@ int rtc_load_cmat(rtc_handle* h, const void* M, int32_t nact, int32_t nslopes, i
         RTC_CUDA(h, cudaMemcpy2D(h->d_M, static_cast<size_t>(h->kpad) * esz, M,
                                  static_cast<size_t>(nslopes) * esz, static_cast<size_t>(nslopes) * esz,
                                  nact, cudaMemcpyHostToDevice));
-        if (store == RTC_FP8_E4M3)
+        if (scaled)
             RTC_CUDA(h, cudaMemcpy(h->d_scale, row_scales, nact * sizeof(float), cudaMemcpyHostToDevice));
     } else {
         float* staging = nullptr;
@@ -423,6 +425,8 @@ int rtc_load_predictor(rtc_handle* h, const float* params, int64_t n, float sigm
     if (!params || n != RTC_MLP_NPARAMS || !(sigma > 0.f) || !isfinite(sigma))
         return fail(h, RTC_EINVAL, "need RTC_MLP_NPARAMS parameters and sigma > 0");
     if (h->cfg.n_wfs != 1) return fail(h, RTC_EINVAL, "the predictor is for single-WFS handles");
+    if (h->kpad > 16384)   // the fused kernels keep the slope vector in shared memory
+        return fail(h, RTC_EINVAL, "the predictor supports up to 16384 slopes");
     for (int64_t i = 0; i < n; ++i)
         if (!isfinite(params[i])) return fail(h, RTC_EINVAL, "parameters must be finite");
     DeviceScope ds(h->cfg.device);
@@ -480,7 +484,7 @@ int rtc_get_info(const rtc_handle* h, rtc_info* out) {
     out->ksplit = h->ksplit;
     const int64_t entries = static_cast<int64_t>(h->cfg.nact) * h->nslopes;
     int64_t mb = 0;
-    if (h->store >= 0) mb = entries * dtype_size(h->store) + (h->store == RTC_FP8_E4M3 ? 4LL * h->cfg.nact : 0);
+    if (h->store >= 0) mb = entries * dtype_size(h->store) + (h->store == RTC_FP8_E4M3 || h->store == RTC_INT8 ? 4LL * h->cfg.nact : 0);
     out->matrix_bytes = mb;
     out->frame_bytes = static_cast<int64_t>(h->cfg.n_wfs) * h->side * h->side * 2;
     out->calib_bytes = 2LL * 4 * h->cfg.n_wfs * h->n_valid * h->cfg.npx * h->cfg.npx;
@@ -494,11 +498,12 @@ int rtc_process_frame(rtc_handle* h, const uint16_t* frame, float* dm_out, float
     DeviceScope ds(h->cfg.device);
     const size_t fbytes = static_cast<size_t>(h->cfg.n_wfs) * h->side * h->side * sizeof(uint16_t);
     RTC_CUDA(h, cudaMemcpyAsync(h->d_frame, frame, fbytes, cudaMemcpyHostToDevice, h->stream));
-    rc = enqueue_step(h, h->d_frame, nullptr, nullptr, h->stream);
+    const float* s_used = nullptr;
+    rc = enqueue_step(h, h->d_frame, nullptr, nullptr, h->stream, &s_used);
     if (rc != RTC_OK) return rc;
     RTC_CUDA(h, cudaMemcpyAsync(dm_out, h->d_a, h->cfg.nact * sizeof(float), cudaMemcpyDeviceToHost, h->stream));
     if (slopes_out)
-        RTC_CUDA(h, cudaMemcpyAsync(slopes_out, h->d_s, h->nslopes * sizeof(float), cudaMemcpyDeviceToHost, h->stream));
+        RTC_CUDA(h, cudaMemcpyAsync(slopes_out, s_used, h->nslopes * sizeof(float), cudaMemcpyDeviceToHost, h->stream));
     return take_status(h, h->stream);
 }
 

@@ -112,7 +112,11 @@ cudaError_t frame_kernel_configure();
 // Persistent loop kernel (see loop_kernel.cu).
 cudaError_t loop_kernel_configure();
 cudaError_t launch_loop(rtc_handle* h, const LoopLaunch& ll, cudaStream_t st);
-cudaError_t launch_frame(rtc_handle* h, const uint16_t* d_frame, float* d_dm_out, cudaStream_t st);
+// One frame through the fused kernel.  d_s_meas == nullptr: the plain path (slopes in
+// h->d_s).  Otherwise the predictor path: measured slopes into d_s_meas = ring row
+// `head` of h->d_ring, predicted slopes into h->d_spred, reconstruction from those.
+cudaError_t launch_frame(rtc_handle* h, const uint16_t* d_frame, float* d_dm_out, float* d_s_meas,
+                         int head, cudaStream_t st);
 cudaError_t launch_mvm_integrate(const rtc_handle* h, const float* d_s, float* d_dm_out,
                                  cudaStream_t st);
 

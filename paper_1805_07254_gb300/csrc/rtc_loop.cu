@@ -224,6 +224,9 @@ extern "C" int rtc_run_loop(rtc_handle* h, const rtc_loop_config* cfg, rtc_stats
     LOOP_CUDA(cudaStreamSynchronize(h->stream));
     h->grid_epoch = 0;
 
+    // with the predictor on, every frame the kernel took pushed one measured vector
+    // into the history ring
+    if (h->pred_on) h->ring_head = static_cast<int>((h->ring_head + e2e.size()) & 3);
     stats->frames = e2e.size();
     if (!e2e.empty() && t_last_done > t_first_pub)
         stats->frames_per_s = e2e.size() / ((t_last_done - t_first_pub) / 1e9);

@@ -16,7 +16,7 @@ PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(PKG, "librtc.so")
 
 RTC_OK, RTC_EINVAL, RTC_ENOMEM, RTC_EDEVICE, RTC_ETIMEDOUT, RTC_ESTATE, RTC_EBUSY = 0, -1, -2, -3, -4, -5, -6
-DTYPES = {"f32": 0, "bf16": 1, "fp8": 2}
+DTYPES = {"f32": 0, "bf16": 1, "fp8": 2, "f16": 3, "int8": 4}
 _ERRNAMES = {0: "RTC_OK", -1: "RTC_EINVAL", -2: "RTC_ENOMEM", -3: "RTC_EDEVICE",
              -4: "RTC_ETIMEDOUT", -5: "RTC_ESTATE", -6: "RTC_EBUSY"}
 
@@ -138,11 +138,18 @@ def _ptr(x):
     raise TypeError(f"cannot pass {type(x)} to librtc")
 
 
+# cudaStreamLegacy: the legacy default stream as an explicit handle.  A torch stream
+# object whose handle is 0 (torch's default stream) is passed as this, because a
+# NULL stream means "the handle's own stream" to the library.
+_CUDA_STREAM_LEGACY = 1
+
+
 def _stream_ptr(stream):
+    """cudaStream_t for a torch stream, a raw handle, or None (the library default)."""
     if stream is None:
         return None
     if hasattr(stream, "cuda_stream"):
-        return stream.cuda_stream
+        return stream.cuda_stream or _CUDA_STREAM_LEGACY
     return int(stream)
 
 
@@ -212,8 +219,12 @@ class Rtc:
             m = np.ascontiguousarray(M, dtype=np.float32)
         elif src == "bf16":
             m = np.ascontiguousarray(M, dtype=np.uint16)
+        elif src == "f16":
+            m = np.ascontiguousarray(M, dtype=np.float16)
         elif src == "fp8":
             m = np.ascontiguousarray(M, dtype=np.uint8)
+        elif src == "int8":
+            m = np.ascontiguousarray(M, dtype=np.int8)
         else:
             raise ValueError(src)
         sc = None if row_scales is None else np.ascontiguousarray(row_scales, dtype=np.float32)

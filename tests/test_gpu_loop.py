@@ -31,7 +31,7 @@ def _per_frame_reference(r, frames, n):
     return out
 
 
-@pytest.mark.parametrize("store", ["f32", "bf16", "fp8"])
+@pytest.mark.parametrize("store", ["f32", "bf16", "f16", "fp8", "int8"])
 def test_loop_equals_per_frame_path(store):
     cfg = synth.elt_scao()
     frames, _ = synth.make_frames(cfg, 0, 4)
@@ -47,6 +47,33 @@ def test_loop_equals_per_frame_path(store):
         np.testing.assert_array_equal(got[k], ref[k])
     np.testing.assert_array_equal(r1.get_dm(), ref[-1])
     assert np.all(e2e > 0) and np.all(dev > 0) and np.all(dev <= e2e)
+
+
+def test_loop_with_predictor_equals_per_frame_path():
+    """BF16 matrix + learned predictor: the loop kernel's frames are the per-frame
+    kernel's, bit for bit, and both leave the same history behind."""
+    from synth.mlp_init import flatten, init_mlp_params
+    cfg = synth.elt_scao()
+    frames, _ = synth.make_frames(cfg, 0, 4)
+    frames = frames.numpy()
+    n = 10
+    params = flatten(init_mlp_params(5))
+    r1, *_ = make_pair(cfg, store="bf16")
+    r2, *_ = make_pair(cfg, store="bf16")
+    for r in (r1, r2):
+        r.load_predictor(params, 0.3)
+        r.set_predictor(True)
+    got = {}
+    stats, _, _ = r1.run_loop(n, frames=frames, sink=lambda k, dm: got.__setitem__(k, dm))
+    assert stats["frames"] == n
+    ref = _per_frame_reference(r2, frames, n)
+    for k in range(n):
+        np.testing.assert_array_equal(got[k], ref[k])
+    # the history carries over from the loop into the per-frame path
+    ref2 = _per_frame_reference(r2, frames[::-1].copy(), 3)
+    got2 = _per_frame_reference(r1, frames[::-1].copy(), 3)
+    for a, b in zip(got2, ref2):
+        np.testing.assert_array_equal(a, b)
 
 
 def test_loop_tiny_against_oracle():

@@ -200,3 +200,46 @@ def test_handle_predictor_path_matches_oracle():
     dm = r.process_frame(frames[0])
     a_ref, _ = oracle.step(frames[0])
     assert rel_rms(dm, a_ref) <= 1e-5
+
+
+@pytest.mark.parametrize("cfg_name", ["tiny", "elt"])
+def test_fused_prediction_equals_standalone_kernels(cfg_name):
+    """The prediction inside the fused frame kernel is the stand-alone predictor's, bit
+    for bit: a handle with the predictor on gives the DM commands of a plain handle
+    that reconstructs from rtc_mlp_predict_seq's predictions of the slopes the first
+    handle measured."""
+    from paper_1805_07254_gb300 import Mlp
+    cfg = synth.CONFIGS[cfg_name]()
+    n = 7
+    frames, _ = synth.make_frames(cfg, 0, n)
+    r1, *_ = make_pair(cfg, store="bf16")
+    r2, *_ = make_pair(cfg, store="bf16")
+    params = flatten(init_mlp_params(21))
+    sigma = 0.25
+    r1.load_predictor(params, sigma)
+    r1.set_predictor(True)
+    nv, nslopes = cfg.subaps.shape[0], cfg.nslopes
+    st = torch.cuda.current_stream()
+    d_frames = frames.to(DEV)
+    dm1 = torch.zeros((n, cfg.nact), device=DEV)
+    s1 = torch.zeros((n, nslopes), device=DEV)
+    for k in range(n):
+        r1.process_frame_async(d_frames[k], dm1[k], s1[k], stream=st)
+    # the measured slopes the fused path reported, after 3 empty history rows
+    S = torch.zeros((n + 4, nslopes), device=DEV)
+    S[3:3 + n] = s1
+    m = Mlp(params=params)
+    m.set_geometry(cfg.subaps, cfg.nsub)
+    P = torch.zeros_like(S)
+    m.predict_seq(S, sigma, P, stream=st)
+    kpad = r2.info()["kpad"]
+    dm2 = torch.zeros((n, cfg.nact), device=DEV)
+    for k in range(n):
+        sp = torch.zeros(kpad, device=DEV)
+        sp[:nslopes] = P[k + 4]
+        r2.reconstruct_async(sp, dm2[k], stream=st)
+        torch.cuda.synchronize()
+    torch.cuda.synchronize()
+    assert nv * 2 == nslopes
+    assert torch.count_nonzero(s1) > 0
+    assert torch.equal(dm1, dm2)

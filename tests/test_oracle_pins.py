@@ -252,6 +252,64 @@ def test_fp8_row_scale_invariants():
     assert np.all(np.isin(np.abs(q), Q.e4m3_values()))
 
 
+def test_f16_format_and_known_roundings():
+    v = Q.f16_values()
+    assert len(v) == 0x7C00 and v[0] == 0.0 and v[-1] == 65504.0
+    assert v[1] == 2.0 ** -24 and v[0x400] == 2.0 ** -14 and v[0x3C00] == 1.0
+    assert np.all(np.diff(v) > 0)
+    # 1 + 2^-11 is a tie between 1 and 1 + 2^-10: even code -> 1; 1 + 3*2^-11 -> 1 + 2^-9
+    cases = {1.0 + 2.0 ** -11: 1.0, 1.0 + 3 * 2.0 ** -11: 1.0 + 2.0 ** -9, 65519.0: 65504.0,
+             65520.0: np.inf, -1e6: -np.inf, 2.0 ** -25: 0.0, 3 * 2.0 ** -25: 2.0 ** -23,
+             0.1: 0.0999755859375}
+    for x, want in cases.items():
+        assert Q.f16_round(x) == want, (x, Q.f16_round(x), want)
+
+
+def test_f16_round_matches_libraries():
+    rng = np.random.default_rng(5)
+    v = Q.f16_values()
+    x = np.concatenate([rng.standard_normal(4000) * 0.011, rng.uniform(-6e4, 6e4, 2000),
+                        rng.standard_normal(2000) * 1e-6, v[::97], -v[::89],
+                        (v[1::61] + v[:-1:61]) / 2]).astype(np.float32)
+    mine = Q.f16_round(x)
+    np.testing.assert_array_equal(mine, x.astype(np.float16).astype(np.float64))
+    np.testing.assert_array_equal(mine, torch.from_numpy(x).half().double().numpy())
+
+
+def test_int8_row_quantise_invariants_and_ties():
+    rng = np.random.default_rng(6)
+    M = (rng.standard_normal((40, 500)) / math.sqrt(500)).astype(np.float32)
+    M[3] = 0.0
+    q, sc = Q.int8_row_quantise(M)
+    assert sc[3] == 1.0 and np.all(q[3] == 0)
+    rows = [r for r in range(40) if r != 3]
+    amax_idx = np.argmax(np.abs(M[rows]), axis=1)
+    assert np.all(np.abs(q[rows, amax_idx]) == 127.0)
+    assert np.all(q == np.round(q)) and np.all(np.abs(q) <= 127.0)
+    deq = Q.stored_matrix(M, "int8")
+    # each entry within half a step of its row's grid
+    assert np.all(np.abs(deq - M) <= 0.5 * sc[:, None].astype(np.float64) * (1 + 1e-6))
+    # a row whose maximum is 127 has scale 1, so the codes are the entries rounded
+    # half to even: 2.5 -> 2, 3.5 -> 4, -2.5 -> -2, 0.5 -> 0, 126.5 -> 126
+    row = np.array([[127.0, 2.5, 3.5, -2.5, 0.5, 126.5, -127.0, 1.49]], np.float32)
+    q1, s1 = Q.int8_row_quantise(row)
+    assert s1[0] == 1.0
+    np.testing.assert_array_equal(q1[0], [127, 2, 4, -2, 0, 126, -127, 1])
+
+
+def test_reduced_precision_errors_are_ordered():
+    """Relative RMS error of M s for the stored formats on an ELT-shaped block:
+    FP16 < BF16 < INT8 < FP8, with FP16 and BF16 inside 2e-3 and INT8 inside 2e-2."""
+    rng = np.random.default_rng(7)
+    M = (rng.standard_normal((256, 8000)) / math.sqrt(8000)).astype(np.float32)
+    s = rng.standard_normal(8000) * 0.3
+    d = M.astype(np.float64) @ s
+    err = {k: np.sqrt(np.mean((Q.stored_matrix(M, k) @ s - d) ** 2) / np.mean(d ** 2))
+           for k in ("f16", "bf16", "int8", "fp8")}
+    assert err["f16"] < err["bf16"] < err["int8"] < err["fp8"], err
+    assert err["f16"] <= 2e-3 and err["bf16"] <= 2e-3 and err["int8"] <= 2e-2, err
+
+
 # --------------------------------------------------------------------- predictor MLP
 def test_gelu_matches_library_erf():
     z = np.linspace(-6, 6, 101)
