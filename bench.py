@@ -48,7 +48,6 @@ def parse_args(argv=None):
     ap.add_argument("--warmup", type=int, default=50)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--store", choices=["f32", "bf16", "f16", "fp8", "int8"], default="f32")
-    ap.add_argument("--ksplit", type=int, default=0)
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-loop", action="store_true")
     ap.add_argument("--loop-frames", type=int, default=2000)
@@ -88,7 +87,7 @@ def measured_peaks():
         return FALLBACK_HBM_GBS, "fallback"
 
 
-KERNEL_SOURCES = ("frame_kernel.cu", "stream_mvm.cuh", "pixel.cuh")
+KERNEL_SOURCES = ("frame_kernel.cu", "stream_mvm.cuh", "pixel.cuh", "pred_tile.cuh")
 
 
 def kernel_source_digest():
@@ -227,7 +226,8 @@ def workload_config(cfg, store, info=None):
          "nslopes": cfg.nslopes, "nact": cfg.nact, "matrix_store": store,
          "l2": f"flushed between timed steps (read of a {L2_FLUSH_BYTES >> 20} MiB device buffer, outside the events)"}
     if info:
-        c["ksplit"] = info["ksplit"]
+        c["launch"] = {"blocks": info["blocks"], "tile_chunks": info["tile_chunks"],
+                       "ring_stages": info["ring_stages"]}
     return c
 
 
@@ -277,6 +277,24 @@ def time_steps(torch, r, d_frames, d_dm, flush, st, n_steps, n_warm, fused=True)
     return cog, mvm, step
 
 
+REPLICA_STATS = ("p50", "p99", "p999", "rms_jitter", "peak_to_peak", "mean")
+
+
+def reduce_replicas(torch, dist, stats, device):
+    """Replicas (one controller per GPU): every latency statistic becomes its maximum
+    over the ranks (the worst replica), frames/s the sum of the ranks' 1e6 / mean.
+    dist is torch.distributed with a process group, or None for one rank."""
+    vals = [float(stats[k]) for k in REPLICA_STATS]
+    fps = 1e6 / float(stats["mean"])
+    if dist is not None:
+        t = torch.tensor(vals, device=device, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        f = torch.tensor([fps], device=device, dtype=torch.float64)
+        dist.all_reduce(f, op=dist.ReduceOp.SUM)
+        vals, fps = t.tolist(), float(f[0])
+    return dict(zip(REPLICA_STATS, vals)), fps
+
+
 def ours(args):
     import numpy as np
     import torch
@@ -302,7 +320,7 @@ def ours(args):
 
     def controller(store):
         r = Rtc(cfg.nsub, cfg.npx, cfg.nact, obs=cfg.obs, gain=cfg.gain, leak=cfg.leak,
-                device=local, ksplit=args.ksplit)
+                device=local)
         r.load_calib(dark, flat)
         r.load_cmat(M, store=store)
         return r
@@ -447,12 +465,9 @@ def ours(args):
                 "dev_rms_jitter_us": round(st_l["dev_rms_jitter_us"], 3)}
             rl.close()
 
-    # max over ranks (worst replica)
-    value = s_step["p50"]
-    if world > 1:
-        t = torch.tensor([value, s_step["p99"]], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        value = float(t[0])
+    # replicas: the worst replica's latency statistics, the aggregate frames/s
+    worst, total_fps = reduce_replicas(torch, dist if world > 1 else None, s_step, dev)
+    value = worst["p50"]
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -468,10 +483,10 @@ def ours(args):
         "ms_per_step": round(s_step["mean"] / 1e3, 6), "higher_is_better": False,
         "scaling": "weak", "vs_baseline": None, "dtype": args.store, "data": "synthetic",
         "config": workload_config(cfg, args.store, info),
-        "p50_us": round(s_step["p50"], 3), "p99_us": round(s_step["p99"], 3),
-        "p999_us": round(s_step["p999"], 3), "rms_jitter_us": round(s_step["rms_jitter"], 3),
-        "peak_to_peak_us": round(s_step["peak_to_peak"], 3), "mean_us": round(s_step["mean"], 3),
-        "frames_per_s": round(world * 1e6 / s_step["mean"], 1),
+        "p50_us": round(worst["p50"], 3), "p99_us": round(worst["p99"], 3),
+        "p999_us": round(worst["p999"], 3), "rms_jitter_us": round(worst["rms_jitter"], 3),
+        "peak_to_peak_us": round(worst["peak_to_peak"], 3), "mean_us": round(worst["mean"], 3),
+        "frames_per_s": round(total_fps, 1),
         "stage_path_us_p50": {"calib_cog_kernel": round(s_cog["p50"], 3),
                               "mvm_stream_kernel": round(s_mvm["p50"], 3),
                               "step_two_kernels": round(s_step2["p50"], 3)},

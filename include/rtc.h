@@ -70,7 +70,6 @@ typedef struct rtc_config {
     int32_t thr_mode;   /* 0: p < thr -> 0;  1: p -> max(p - thr, 0) */
     float   thr;        /* threshold in calibrated ADU */
     int32_t device;     /* CUDA device ordinal */
-    int32_t ksplit;     /* MVM split-K factor; 0 chooses automatically */
     int32_t reserved;   /* must be 0 */
 } rtc_config;
 
@@ -80,7 +79,11 @@ typedef struct rtc_info {
     int32_t nact;
     int32_t kpad;           /* matrix row length after padding to a multiple of 16 */
     int32_t store;          /* rtc_dtype of the loaded matrix, -1 if none */
-    int32_t ksplit;         /* split-K factor in use */
+    /* launch plan of the fused kernels for the loaded matrix (0 while none):  */
+    int32_t blocks;         /* blocks, one per SM, each streaming an equal share */
+    int32_t tile_chunks;    /* 16-byte chunks per matrix row in one streamed tile */
+    int32_t ring_stages;    /* tiles in flight per consumer team */
+    int32_t reserved;
     int64_t matrix_bytes;   /* algorithmic bytes of the stored matrix (unpadded, incl. scales) */
     int64_t frame_bytes;    /* n_wfs * H * W * 2 */
     int64_t calib_bytes;    /* bytes of the per-pixel calibration data read per frame */

@@ -12,7 +12,9 @@
 #include <vector>
 
 #include "mlp.h"
+#include "pred_tile.cuh"
 #include "rtc_internal.h"
+#include "stream_mvm.cuh"
 
 namespace {
 
@@ -94,11 +96,6 @@ std::vector<int32_t> default_subaps(int n, float obs) {
             }
         }
     return rc;
-}
-
-int choose_ksplit(const rtc_handle* h) {
-    if (h->cfg.ksplit > 0) return std::min(h->cfg.ksplit, kMaxKsplit);
-    return 1;
 }
 
 // (Re)build everything whose size depends on the subaperture map.
@@ -215,7 +212,6 @@ int rtc_create(const rtc_config* cfg, rtc_handle** out) {
     if (!isfinite(c.gain) || !isfinite(c.leak) || !isfinite(c.thr))
         return fail(nullptr, RTC_EINVAL, "gain, leak and thr must be finite");
     if (c.thr_mode != 0 && c.thr_mode != 1) return fail(nullptr, RTC_EINVAL, "thr_mode must be 0 or 1");
-    if (c.ksplit < 0) return fail(nullptr, RTC_EINVAL, "ksplit must be >= 0");
     if (c.reserved != 0) return fail(nullptr, RTC_EINVAL, "reserved must be 0");
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || c.device < 0 || c.device >= ndev)
@@ -228,7 +224,6 @@ int rtc_create(const rtc_config* cfg, rtc_handle** out) {
     h->leak = c.leak;
     h->thr_mode = c.thr_mode;
     h->thr = c.thr;
-    h->ksplit = choose_ksplit(h);
     DeviceScope ds(c.device);
     int rcode = RTC_OK;
     cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, c.device);
@@ -481,7 +476,14 @@ int rtc_get_info(const rtc_handle* h, rtc_info* out) {
     out->nact = h->cfg.nact;
     out->kpad = h->kpad;
     out->store = h->store;
-    out->ksplit = h->ksplit;
+    out->blocks = out->tile_chunks = out->ring_stages = out->reserved = 0;
+    if (h->store >= 0 && h->kpad > 0) {
+        const rtc_mvm::Launch L = rtc_mvm::plan_launch(h, 16 / dtype_size(h->store),
+                                                       h->pred_on ? rtc_pred::kSmemBytes : 0);
+        out->blocks = L.G;
+        out->tile_chunks = L.tw;
+        out->ring_stages = L.nst;
+    }
     const int64_t entries = static_cast<int64_t>(h->cfg.nact) * h->nslopes;
     int64_t mb = 0;
     if (h->store >= 0) mb = entries * dtype_size(h->store) + (h->store == RTC_FP8_E4M3 || h->store == RTC_INT8 ? 4LL * h->cfg.nact : 0);

@@ -43,7 +43,6 @@ struct rtc_handle {
     int nslopes = 0;            // 2 * n_valid * n_wfs
     int kpad = 0;               // padded matrix row length (elements)
     int store = -1;             // rtc_dtype of the resident matrix, -1 when none
-    int ksplit = 1;
     float gain = 0.f, leak = 1.f;
     int thr_mode = 0;
     float thr = 0.f;

@@ -25,12 +25,13 @@ class RtcConfig(C.Structure):
     _fields_ = [("nsub", C.c_int32), ("npx", C.c_int32), ("n_wfs", C.c_int32), ("nact", C.c_int32),
                 ("obs", C.c_float), ("gain", C.c_float), ("leak", C.c_float),
                 ("thr_mode", C.c_int32), ("thr", C.c_float), ("device", C.c_int32),
-                ("ksplit", C.c_int32), ("reserved", C.c_int32)]
+                ("reserved", C.c_int32)]
 
 
 class RtcInfo(C.Structure):
     _fields_ = [("n_valid", C.c_int32), ("nslopes", C.c_int32), ("nact", C.c_int32),
-                ("kpad", C.c_int32), ("store", C.c_int32), ("ksplit", C.c_int32),
+                ("kpad", C.c_int32), ("store", C.c_int32), ("blocks", C.c_int32),
+                ("tile_chunks", C.c_int32), ("ring_stages", C.c_int32), ("reserved", C.c_int32),
                 ("matrix_bytes", C.c_int64), ("frame_bytes", C.c_int64), ("calib_bytes", C.c_int64)]
 
 
@@ -158,9 +159,9 @@ class Rtc:
 
     def __init__(self, nsub: int, npx: int, nact: int, n_wfs: int = 1, obs: float = 0.0,
                  gain: float = 0.4, leak: float = 0.99, thr_mode: int = 0, thr: float = 0.0,
-                 device: int = 0, ksplit: int = 0):
+                 device: int = 0):
         self._lib = load_library()
-        cfg = RtcConfig(nsub, npx, n_wfs, nact, obs, gain, leak, thr_mode, thr, device, ksplit, 0)
+        cfg = RtcConfig(nsub, npx, n_wfs, nact, obs, gain, leak, thr_mode, thr, device, 0)
         h = _P()
         rc = self._lib.rtc_create(C.byref(cfg), C.byref(h))
         if rc != RTC_OK:

@@ -15,7 +15,7 @@ def rel_rms(x, ref):
     return float(np.sqrt(np.mean((x - ref) ** 2)) / (den if den > 0 else 1.0))
 
 
-def make_pair(cfg, store="f32", thr_mode=0, thr=0.0, ksplit=0, subaps=None, M=None, device=0):
+def make_pair(cfg, store="f32", thr_mode=0, thr=0.0, subaps=None, M=None, device=0):
     """Device controller and FP64 oracle loop set up from the same seeded inputs."""
     from paper_1805_07254_gb300 import Rtc
     dark, flat = synth.calibration_maps(cfg)
@@ -24,7 +24,7 @@ def make_pair(cfg, store="f32", thr_mode=0, thr=0.0, ksplit=0, subaps=None, M=No
     if M is None:
         M = synth.control_matrix(cfg, nslopes=2 * sa.shape[0] * cfg.n_wfs).numpy()
     r = Rtc(cfg.nsub, cfg.npx, cfg.nact, n_wfs=cfg.n_wfs, obs=cfg.obs, gain=cfg.gain,
-            leak=cfg.leak, thr_mode=thr_mode, thr=thr, device=device, ksplit=ksplit)
+            leak=cfg.leak, thr_mode=thr_mode, thr=thr, device=device)
     if subaps is not None:
         r.load_subaps(sa)
     r.load_calib(dark, flat)

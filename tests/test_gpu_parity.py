@@ -48,13 +48,25 @@ def test_tiny_scao_closed_loop_1000_frames():
     _run_and_compare(r, oracle, frames.numpy())
 
 
-@pytest.mark.parametrize("ksplit", [1, 2, 3, 7, 32])
-def test_split_k_factors_agree(ksplit):
-    cfg = synth.tiny_scao()
-    frames, _ = synth.make_frames(cfg, 0, 20)
-    r, oracle, *_ = make_pair(cfg, ksplit=ksplit)
-    assert r.info()["ksplit"] == ksplit
-    _run_and_compare(r, oracle, frames.numpy())
+@pytest.mark.parametrize("store", ["f32", "bf16", "f16", "fp8", "int8"])
+def test_launch_plan_streams_equal_tiles(store):
+    """One block per SM (at most one per row group); rows split into equal tiles of
+    at most 448 chunks; rings of 2..8 stages; the plan covers every row chunk."""
+    cfg = synth.elt_scao()
+    r, *_ = make_pair(cfg, store=store)
+    info = r.info()
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    assert info["blocks"] == min(sms, (cfg.nact + 3) // 4)
+    epc = {"f32": 4, "bf16": 8, "f16": 8, "fp8": 16, "int8": 16}[store]
+    cpr = info["kpad"] // epc
+    tw = info["tile_chunks"]
+    ntile = -(-cpr // tw)
+    assert 0 < tw <= 448 and ntile == -(-cpr // 448) and tw * ntile - cpr < ntile
+    assert 2 <= info["ring_stages"] <= 8
+    # a short row gets a deeper ring than a long one
+    if store in ("fp8", "int8"):
+        r32, *_ = make_pair(cfg, store="f32")
+        assert info["ring_stages"] > r32.info()["ring_stages"]
 
 
 @pytest.mark.parametrize("mode,thr", [(0, 5.0), (1, 5.0), (0, -1e9), (1, 40.0)])

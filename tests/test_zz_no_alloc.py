@@ -45,7 +45,7 @@ def test_noalloc_matches_handle_path_on_two_calls(store):
     slopes = [(0.3 * rng.standard_normal(ns)).astype(np.float32) for _ in range(2)]
     dev = torch.device("cuda:0")
 
-    r = Rtc(cfg.nsub, cfg.npx, nact, obs=cfg.obs, gain=cfg.gain, leak=cfg.leak, ksplit=ksplit)
+    r = Rtc(cfg.nsub, cfg.npx, nact, obs=cfg.obs, gain=cfg.gain, leak=cfg.leak)
     r.load_cmat(M, store=store)
 
     # caller-owned buffers in the stored layout: [nact][kpad], zero padded
