@@ -226,8 +226,8 @@ def workload_config(cfg, store, info=None):
          "nslopes": cfg.nslopes, "nact": cfg.nact, "matrix_store": store,
          "l2": f"flushed between timed steps (read of a {L2_FLUSH_BYTES >> 20} MiB device buffer, outside the events)"}
     if info:
-        c["launch"] = {"blocks": info["blocks"], "tile_chunks": info["tile_chunks"],
-                       "ring_stages": info["ring_stages"]}
+        c["launch"] = {"slices": info["slices"], "blocks": info["blocks"],
+                       "tile_rows": info["tile_rows"], "ring_stages": info["ring_stages"]}
     return c
 
 

@@ -79,11 +79,12 @@ typedef struct rtc_info {
     int32_t nact;
     int32_t kpad;           /* matrix row length after padding to a multiple of 16 */
     int32_t store;          /* rtc_dtype of the loaded matrix, -1 if none */
-    /* launch plan of the fused kernels for the loaded matrix (0 while none):  */
-    int32_t blocks;         /* blocks, one per SM, each streaming an equal share */
-    int32_t tile_chunks;    /* 16-byte chunks per matrix row in one streamed tile */
-    int32_t ring_stages;    /* tiles in flight per consumer team */
-    int32_t reserved;
+    /* layout and launch plan of the loaded matrix (0 while none): */
+    int32_t slices;         /* column slices (consecutive subapertures), each stored
+                               contiguously and multiplied by one block */
+    int32_t blocks;         /* blocks of the fused kernels, one per SM */
+    int32_t tile_rows;      /* matrix rows per streamed tile */
+    int32_t ring_stages;    /* tiles in flight per block */
     int64_t matrix_bytes;   /* algorithmic bytes of the stored matrix (unpadded, incl. scales) */
     int64_t frame_bytes;    /* n_wfs * H * W * 2 */
     int64_t calib_bytes;    /* bytes of the per-pixel calibration data read per frame */

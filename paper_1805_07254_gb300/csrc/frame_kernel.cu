@@ -1,18 +1,25 @@
 // Fused frame kernel: the whole per-frame pipeline of Sec. 2.1 / Fig. 3 in one
 // cooperative launch.
 //
-// While the producer warps of every block start streaming matrix tiles into
-// shared memory (the matrix does not depend on the frame), the consumer warps
-// compute the block's share of the slopes (pixel.cuh); a bounded grid barrier then
-// makes the whole slope vector visible, and the consumers run the streaming
-// reconstruction and integrator (stream_mvm.cuh).  The pixel work and the
-// launch of the reconstruction are hidden under the first matrix tiles, much as
-// DARC's horizontal processing overlaps work with pixel arrival (Sec. 2.2).
+// Each block owns a run of matrix slices (stream_mvm.cuh) and the subapertures
+// whose slopes those slices multiply.  While its producer warp streams the slices'
+// matrix tiles into shared memory (the matrix does not depend on the frame), the
+// consumer warps compute the block's slopes (pixel.cuh) into shared memory and
+// multiply them straight away: no block waits for another before its share of the
+// product, as in the paper's per-thread column blocks (Sec. 2.3).  Each block
+// writes one partial DM vector per slice; a bounded grid barrier then lets every
+// block sum its share of the rows over the slices in a fixed order and apply the
+// integrator (the partial-DM-vector tree of Sec. 2.3.5).
+//
+// The pixel loads are on the frame's critical path: the producer warp waits on a
+// named barrier until every consumer warp has issued its first pixel loads, streams
+// one tile, and holds the rest until the block's slopes are known, so that the pixel
+// loads do not queue behind a flood of bulk copies.
 //
 // With the learned slope predictor on (PRED), the measured slopes go into the
-// history ring, a second phase between two grid barriers predicts the next
-// slopes of every subaperture (pred_tile.cuh, in the shared memory the slope copy
-// takes later), and the reconstruction multiplies the prediction.
+// history ring, a grid barrier makes them visible, each block predicts the next
+// slopes of its own subapertures from their neighbourhoods (pred_tile.cuh, in the
+// shared scratch before the slopes) and multiplies the prediction.
 //
 // The grid barrier counts block arrivals on a 64-bit counter that only grows;
 // each barrier waits for the running total of arrivals expected up to and
@@ -30,15 +37,12 @@ namespace {
 using namespace rtc_mvm;
 
 // Named barrier on which the producer warp waits until every consumer warp has
-// issued its first pixel loads: the matrix prefetch fills the memory system for
-// microseconds, and pixel loads queued behind it would delay the whole frame.
+// issued its first pixel loads.
 constexpr int kGateBar = 4;
-// Matrix tiles each team's producer streams before the slopes are known; the rest
-// follows once they are (a flood of bulk copies would slow the pixel loads and the
-// grid barrier's round trips, which are on the frame's critical path).
+// Matrix tiles the producer streams before the block's slopes are known.
 constexpr int kPrefetchTiles = 1;
 
-template <int DT, bool S_SMEM, int NPX, bool PRED>
+template <int DT, int NPX, bool PRED>
 __global__ void __launch_bounds__(kThreads, 1)
 frame_kernel(rtc_pixel::PixelArgs px, Args g, rtc_pred::PredArgs pa, int head,
              unsigned long long* gridbar, unsigned long long target) {
@@ -47,17 +51,17 @@ frame_kernel(rtc_pixel::PixelArgs px, Args g, rtc_pred::PredArgs pa, int head,
     const int tid = threadIdx.x;
     if (tid == 0) init_shared(sh);
     __syncthreads();
-    const Plan pl = make_plan<DT, S_SMEM>(g, smem);
+    const Plan pl = make_plan(g, smem);
     if (tid >= kConsumers) {
         asm volatile("bar.sync %0, %1;" ::"n"(kGateBar), "n"(kThreads) : "memory");
-        if ((tid & 31) < kTeams) produce(g, pl, sh, tid & 31, 0, true, kPrefetchTiles);
+        if ((tid & 31) == 0) produce(g, pl, sh, 0, true, kPrefetchTiles);
         return;
     }
-    // pixel stage: this block's share of the subapertures, one half-warp each (so
-    // the ~26 subapertures of a block on the ELT frame take a single round)
-    const int nt = px.n_valid * px.n_wfs;
-    const int i0 = static_cast<int>(static_cast<long long>(nt) * blockIdx.x / gridDim.x);
-    const int i1 = static_cast<int>(static_cast<long long>(nt) * (blockIdx.x + 1) / gridDim.x);
+    clear_local(g, pl, tid);
+    consumer_sync();
+
+    // pixel stage: the block's subapertures, one half-warp each (the ~26
+    // subapertures of a block on the ELT frame take a single round)
     const int slot = 2 * (tid >> 5) + ((tid >> 4) & 1);
     bool gate_open = false;             // every consumer warp arrives exactly once
     auto open_gate = [&gate_open]() {
@@ -66,85 +70,95 @@ frame_kernel(rtc_pixel::PixelArgs px, Args g, rtc_pred::PredArgs pa, int head,
             gate_open = true;
         }
     };
-    for (int base = i0; base < i1; base += 2 * kConsumerWarps) {
+    for (int base = pl.g0; base < pl.g1; base += 2 * kConsumerWarps) {
         const int gi = base + slot;
-        rtc_pixel::subap_slopes<NPX, rtc_pixel::kPixelReadOnly, 16>(px, px.frame, px.s, gi, gi < i1,
-                                                                    tid & 31, open_gate);
+        const bool valid = gi < pl.g1;
+        const float2 sxy = rtc_pixel::subap_slopes<NPX, rtc_pixel::kPixelReadOnly, 16>(
+            px, px.frame, px.s, gi, valid, tid & 31, open_gate);
+        if (valid && (tid & 15) == 0) {
+            int ix, iy;
+            local_index(g, pl, gi, ix, iy);
+            pl.loc[ix] = sxy.x;
+            pl.loc[iy] = sxy.y;
+        }
     }
     open_gate();                        // a warp without pixel work
-    // every block's slopes must be visible before any block reads s
-    consumer_sync();
-    if (tid == 0) grid_barrier(gridbar, target, g.status, &sh.abort_flag);
-    consumer_sync();
-    const float* s_vec = g.s;
+    prefetch_rows<DT>(g, pl, tid);
+
+    unsigned long long next = target;   // arrivals that complete the next grid barrier
     if (PRED) {
-        // next slopes of the block's subapertures from the 4 newest measured vectors
-        if (!sh.abort_flag) rtc_pred::predict(pa, pl.scratch, tid, i0, i1, head);
-        if (tid == 0 && !sh.abort_flag)
-            grid_barrier(gridbar, target + gridDim.x, g.status, &sh.abort_flag);
+        // every block's measured slopes in the history ring, then the prediction of
+        // the block's own subapertures, which replaces their local slopes
         consumer_sync();
-        s_vec = pa.s_pred;
+        if (tid == 0) grid_barrier(gridbar, next, g.status, &sh.abort_flag);
+        consumer_sync();
+        next += gridDim.x;
+        if (!sh.abort_flag) {
+            rtc_pred::predict(pa, pl.scratch, tid, pl.g0, pl.g1, head);
+            gather_local(g, pl, tid, pa.s_pred, true);
+        }
     }
-    consumer_prologue<DT, S_SMEM, true>(g, pl, tid, s_vec);
+    consumer_sync();
     if (tid == 0) sh.release = 1;       // the rest of the matrix stream may start
-    consume<DT, S_SMEM, true>(g, pl, sh, tid, 0, s_vec, g.dm_out);
+    consume<DT>(g, pl, sh, tid, 0);
+
+    // every block's partial vectors before any block sums them
+    consumer_sync();
+    if (tid == 0 && !sh.abort_flag) grid_barrier(gridbar, next, g.status, &sh.abort_flag);
+    consumer_sync();
+    if (!sh.abort_flag) reduce_rows<DT>(g, pl, tid, g.dm_out);
 }
 
-template <int DT, bool S, int NPX, bool PRED>
+template <int DT, int NPX, bool PRED>
 cudaError_t launch_t(const Launch& L, rtc_pixel::PixelArgs px, Args g, rtc_pred::PredArgs pa, int head,
                      unsigned long long* bar, unsigned long long target, cudaStream_t st) {
     void* args[] = {&px, &g, &pa, &head, &bar, &target};
-    return cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(frame_kernel<DT, S, NPX, PRED>),
+    return cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(frame_kernel<DT, NPX, PRED>),
                                        dim3(L.G), dim3(kThreads), args, L.smem, st);
 }
 
-template <int DT, bool S, bool PRED>
+template <int DT, bool PRED>
 cudaError_t launch_npx(const rtc_handle* h, const Launch& L, rtc_pixel::PixelArgs px, Args g,
                        rtc_pred::PredArgs pa, int head, unsigned long long target, cudaStream_t st) {
-    if (h->cfg.npx == 10) return launch_t<DT, S, 10, PRED>(L, px, g, pa, head, h->d_gridbar, target, st);
-    return launch_t<DT, S, 0, PRED>(L, px, g, pa, head, h->d_gridbar, target, st);
+    if (h->cfg.npx == 10) return launch_t<DT, 10, PRED>(L, px, g, pa, head, h->d_gridbar, target, st);
+    return launch_t<DT, 0, PRED>(L, px, g, pa, head, h->d_gridbar, target, st);
 }
 
 template <int DT>
 cudaError_t launch_dt(rtc_handle* h, const uint16_t* d_frame, float* d_dm_out, float* d_s_meas,
                       int head, cudaStream_t st) {
     const bool pred = d_s_meas != nullptr;
-    const Launch L = plan_launch(h, Epc<DT>::v, pred ? rtc_pred::kSmemBytes : 0);
-    if (!L.ok || (pred && !L.s_in_smem)) return cudaErrorInvalidValue;
+    const Launch L = plan_launch(h, pred ? rtc_pred::kSmemBytes : 0);
+    if (!L.ok) return cudaErrorInvalidValue;
     const rtc_pixel::PixelArgs px = pixel_args(h, d_frame, pred ? d_s_meas : h->d_s);
-    const Args g = make_args(h, h->d_s, d_dm_out, L, Epc<DT>::v);
+    const Args g = make_args(h, h->d_s, d_dm_out, L);
     // the block count may change between launches (e.g. a server slot limits it), so
     // each target is the running total of expected arrivals, not launches x blocks
     const unsigned long long G = static_cast<unsigned long long>(L.G);
     const unsigned long long target = h->grid_epoch + G;
     cudaError_t e;
     if (pred) {
-        const rtc_pred::PredArgs pa = pred_args(h);
-        e = launch_npx<DT, true, true>(h, L, px, g, pa, head, target, st);
+        e = launch_npx<DT, true>(h, L, px, g, pred_args(h), head, target, st);
     } else {
         const rtc_pred::PredArgs pa{};
-        e = L.s_in_smem ? launch_npx<DT, true, false>(h, L, px, g, pa, 0, target, st)
-                        : launch_npx<DT, false, false>(h, L, px, g, pa, 0, target, st);
+        e = launch_npx<DT, false>(h, L, px, g, pa, 0, target, st);
     }
     if (e == cudaSuccess) h->grid_epoch = target + (pred ? G : 0);
     return e;
 }
 
-template <int DT, bool S, int NPX, bool PRED>
+template <int DT, int NPX, bool PRED>
 cudaError_t configure_t() {
-    return cudaFuncSetAttribute(frame_kernel<DT, S, NPX, PRED>,
-                                cudaFuncAttributeMaxDynamicSharedMemorySize,
+    return cudaFuncSetAttribute(frame_kernel<DT, NPX, PRED>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 static_cast<int>(kDynSmemBudget));
 }
 
 template <int DT>
 cudaError_t configure_dt() {
-    cudaError_t e = configure_t<DT, true, 10, false>();
-    if (e == cudaSuccess) e = configure_t<DT, true, 0, false>();
-    if (e == cudaSuccess) e = configure_t<DT, false, 10, false>();
-    if (e == cudaSuccess) e = configure_t<DT, false, 0, false>();
-    if (e == cudaSuccess) e = configure_t<DT, true, 10, true>();
-    if (e == cudaSuccess) e = configure_t<DT, true, 0, true>();
+    cudaError_t e = configure_t<DT, 10, false>();
+    if (e == cudaSuccess) e = configure_t<DT, 0, false>();
+    if (e == cudaSuccess) e = configure_t<DT, 10, true>();
+    if (e == cudaSuccess) e = configure_t<DT, 0, true>();
     return e;
 }
 

@@ -11,22 +11,23 @@
 //      into a device staging buffer with the widest loads the layout allows
 //      (16 bytes for ELT frames), bypassing the caches (the slot is rewritten
 //      between its uses); a bounded grid barrier makes the whole frame visible,
-//      and the consumers compute the block's share of the slopes from it through
-//      L2 (one coalesced pass over the host link instead of a few scattered
-//      bytes per pixel row);
-//   3. a bounded grid barrier makes the slope vector (double-buffered by frame
-//      parity) visible to all blocks;
-//   3b. with the learned predictor on (PRED), the measured slopes go to the next
-//      row of the handle's history ring instead, the blocks predict the next
-//      slopes of their subapertures (pred_tile.cuh), and a second grid barrier
-//      makes the prediction visible;
-//   4. the streaming reconstruction + integrator; DM commands go to the device
-//      state and to the frame's slot in mapped host memory;
+//      and the consumers compute the slopes of the block's subapertures from it
+//      through L2 into shared memory (one coalesced pass over the host link
+//      instead of a few scattered bytes per pixel row);
+//   3. with the learned predictor on (PRED), the measured slopes go to the next
+//      row of the handle's history ring, a grid barrier makes them visible, and
+//      each block replaces its subapertures' slopes by their prediction
+//      (pred_tile.cuh);
+//   4. each block multiplies its matrix slices by its own slopes (no wait for
+//      other blocks), a grid barrier publishes the partial DM vectors, and each
+//      block sums and integrates its share of the rows (stream_mvm.cuh); DM
+//      commands go to the device state and to the frame's slot in mapped host
+//      memory;
 //   5. the last block to finish publishes the completion record (sequence,
 //      device time the frame was seen, device time the commands were written).
-// The producer warps stream the matrix frame after frame; their barrier phases
+// The producer warp streams the matrix frame after frame; its barrier phases
 // continue across frames, so the next frame's first tiles are already in flight
-// while a frame is being finished.
+// while the kernel waits for the frame.
 
 #include "pixel.cuh"
 #include "pred_tile.cuh"
@@ -69,7 +70,7 @@ __device__ __forceinline__ void st_release_sys(unsigned long long* p, unsigned l
     asm volatile("st.release.sys.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
-template <int DT, bool S_SMEM, int NPX, bool PRED>
+template <int DT, int NPX, bool PRED>
 __global__ void __launch_bounds__(kThreads, 1) loop_kernel(LoopArgs L) {
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ Shared sh;
@@ -81,24 +82,22 @@ __global__ void __launch_bounds__(kThreads, 1) loop_kernel(LoopArgs L) {
     __shared__ Plan pl;
     if (tid == 0) {
         init_shared(sh);
-        pl = make_plan<DT, S_SMEM>(L.mv, smem);
+        pl = make_plan(L.mv, smem);
     }
     __syncthreads();
 
     if (tid >= kConsumers) {
-        // producers: the matrix does not depend on the frame
-        if ((tid & 31) < kTeams) {
-            const int team = tid & 31;
+        // producer: the matrix does not depend on the frame, so the next frame's
+        // first tiles stream while the kernel waits for it
+        if ((tid & 31) == 0) {
             int tl = 0;
             for (unsigned long long k = 0; k < L.n_frames && !sh.abort_flag; ++k)
-                tl = produce(L.mv, pl, sh, team, tl, k + 1 == L.n_frames);
+                tl = produce(L.mv, pl, sh, tl, k + 1 == L.n_frames);
         }
         return;
     }
 
-    const int nt = L.px.n_valid * L.px.n_wfs;
-    const int i0 = static_cast<int>(static_cast<long long>(nt) * blockIdx.x / gridDim.x);
-    const int i1 = static_cast<int>(static_cast<long long>(nt) * (blockIdx.x + 1) / gridDim.x);
+    clear_local(L.mv, pl, tid);         // the padding of the local slopes stays zero
     const int slot_lane = 2 * (tid >> 5) + ((tid >> 4) & 1);
     constexpr unsigned long long kBarriers = PRED ? 3 : 2;     // grid barriers per frame
     // the block's share of the frame's copy units
@@ -126,14 +125,14 @@ __global__ void __launch_bounds__(kThreads, 1) loop_kernel(LoopArgs L) {
                 }
             }
             if (blockIdx.x == 0 && !stop) L.t_seen[k & 1] = global_ns();
-            if (stop) sh.abort_flag = 1;            // the producers stop too
+            if (stop) sh.abort_flag = 1;            // the producer stops too
             stop_now = stop;
         }
         consumer_sync();
         if (stop_now) break;
 
         // 2. the block's share of the frame into device memory, then the block's
-        //    share of the slopes from it
+        //    slopes from it, into the local vector (and the global one)
         const uint16_t* frame = L.frames + static_cast<size_t>(slot) * L.frame_elems;
         if (L.copy_unit == 16) {
             const uint4* src = reinterpret_cast<const uint4*>(frame);
@@ -155,32 +154,40 @@ __global__ void __launch_bounds__(kThreads, 1) loop_kernel(LoopArgs L) {
         const int head = (L.head0 + 1 + static_cast<int>(k & 3)) & 3;
         float* s_k = PRED ? L.pa.ring + static_cast<size_t>(head) * L.kpad
                           : L.s_buf + static_cast<size_t>(k & 1) * L.kpad;
-        for (int base = i0; base < i1; base += 2 * kConsumerWarps) {
+        for (int base = pl.g0; base < pl.g1; base += 2 * kConsumerWarps) {
             const int gi = base + slot_lane;
-            rtc_pixel::subap_slopes<NPX, rtc_pixel::kPixelL2, 16>(L.px, L.stage, s_k, gi, gi < i1,
-                                                                  tid & 31);
+            const bool valid = gi < pl.g1;
+            const float2 sxy = rtc_pixel::subap_slopes<NPX, rtc_pixel::kPixelL2, 16>(
+                L.px, L.stage, s_k, gi, valid, tid & 31);
+            if (valid && (tid & 15) == 0) {
+                int ix, iy;
+                local_index(L.mv, pl, gi, ix, iy);
+                pl.loc[ix] = sxy.x;
+                pl.loc[iy] = sxy.y;
+            }
         }
+        prefetch_rows<DT>(L.mv, pl, tid);
 
-        // 3. the whole slope vector visible to every block
-        consumer_sync();
-        if (tid == 0) grid_barrier(L.gridbar, G * (kBarriers * k + 2), L.mv.status, &sh.abort_flag);
-        consumer_sync();
-        if (sh.abort_flag) break;
-
-        // 3b. predicted next slopes
-        const float* s_vec = s_k;
+        // 3. with the predictor: every block's measured slopes in the history ring,
+        //    then the prediction of the block's own subapertures
         if (PRED) {
-            rtc_pred::predict(L.pa, pl.scratch, tid, i0, i1, head);
-            if (tid == 0) grid_barrier(L.gridbar, G * (kBarriers * k + 3), L.mv.status, &sh.abort_flag);
+            consumer_sync();
+            if (tid == 0) grid_barrier(L.gridbar, G * (kBarriers * k + 2), L.mv.status, &sh.abort_flag);
             consumer_sync();
             if (sh.abort_flag) break;
-            s_vec = L.pa.s_pred;
+            rtc_pred::predict(L.pa, pl.scratch, tid, pl.g0, pl.g1, head);
+            gather_local(L.mv, pl, tid, L.pa.s_pred, true);
         }
+        consumer_sync();
 
-        // 4. reconstruction and integrator
-        consumer_prologue<DT, S_SMEM, true>(L.mv, pl, tid, s_vec);
-        tile = consume<DT, S_SMEM, true>(L.mv, pl, sh, tid, tile, s_vec,
-                                         L.dm_ring + static_cast<size_t>(slot) * L.mv.nact);
+        // 4. the block's partial DM vectors, then its rows summed and integrated;
+        //    DM commands to the device state and the frame's host slot
+        tile = consume<DT>(L.mv, pl, sh, tid, tile);
+        consumer_sync();
+        if (tid == 0) grid_barrier(L.gridbar, G * (kBarriers * k + kBarriers), L.mv.status, &sh.abort_flag);
+        consumer_sync();
+        if (sh.abort_flag) break;
+        reduce_rows<DT>(L.mv, pl, tid, L.dm_ring + static_cast<size_t>(slot) * L.mv.nact);
 
         // 5. the last block to finish publishes the completion record
         consumer_sync();
@@ -198,21 +205,21 @@ __global__ void __launch_bounds__(kThreads, 1) loop_kernel(LoopArgs L) {
     }
 }
 
-template <int DT, bool S, int NPX, bool PRED>
+template <int DT, int NPX, bool PRED>
 cudaError_t launch_t(const Launch& Lc, LoopArgs a, cudaStream_t st) {
     void* args[] = {&a};
-    return cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(loop_kernel<DT, S, NPX, PRED>),
+    return cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(loop_kernel<DT, NPX, PRED>),
                                        dim3(Lc.G), dim3(kThreads), args, Lc.smem, st);
 }
 
 template <int DT>
 cudaError_t launch_dt(rtc_handle* h, const LoopLaunch& ll, cudaStream_t st) {
     const bool pred = h->pred_on;
-    const Launch Lc = plan_launch(h, Epc<DT>::v, pred ? rtc_pred::kSmemBytes : 0);
-    if (!Lc.ok || (pred && !Lc.s_in_smem)) return cudaErrorInvalidValue;
+    const Launch Lc = plan_launch(h, pred ? rtc_pred::kSmemBytes : 0);
+    if (!Lc.ok) return cudaErrorInvalidValue;
     LoopArgs a{};
     a.px = pixel_args(h, nullptr, nullptr);
-    a.mv = make_args(h, nullptr, nullptr, Lc, Epc<DT>::v);
+    a.mv = make_args(h, nullptr, nullptr, Lc);
     a.frames = ll.d_frames;
     a.frame_elems = ll.frame_elems;
     a.stage = h->d_frame;
@@ -233,27 +240,23 @@ cudaError_t launch_dt(rtc_handle* h, const LoopLaunch& ll, cudaStream_t st) {
     if (pred) {
         a.pa = pred_args(h);
         a.head0 = h->ring_head;
-        return npx10 ? launch_t<DT, true, 10, true>(Lc, a, st) : launch_t<DT, true, 0, true>(Lc, a, st);
+        return npx10 ? launch_t<DT, 10, true>(Lc, a, st) : launch_t<DT, 0, true>(Lc, a, st);
     }
-    if (Lc.s_in_smem)
-        return npx10 ? launch_t<DT, true, 10, false>(Lc, a, st) : launch_t<DT, true, 0, false>(Lc, a, st);
-    return npx10 ? launch_t<DT, false, 10, false>(Lc, a, st) : launch_t<DT, false, 0, false>(Lc, a, st);
+    return npx10 ? launch_t<DT, 10, false>(Lc, a, st) : launch_t<DT, 0, false>(Lc, a, st);
 }
 
-template <int DT, bool S, int NPX, bool PRED>
+template <int DT, int NPX, bool PRED>
 cudaError_t configure_t() {
-    return cudaFuncSetAttribute(loop_kernel<DT, S, NPX, PRED>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    return cudaFuncSetAttribute(loop_kernel<DT, NPX, PRED>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 static_cast<int>(kDynSmemBudget));
 }
 
 template <int DT>
 cudaError_t configure_dt() {
-    cudaError_t e = configure_t<DT, true, 10, false>();
-    if (e == cudaSuccess) e = configure_t<DT, true, 0, false>();
-    if (e == cudaSuccess) e = configure_t<DT, false, 10, false>();
-    if (e == cudaSuccess) e = configure_t<DT, false, 0, false>();
-    if (e == cudaSuccess) e = configure_t<DT, true, 10, true>();
-    if (e == cudaSuccess) e = configure_t<DT, true, 0, true>();
+    cudaError_t e = configure_t<DT, 10, false>();
+    if (e == cudaSuccess) e = configure_t<DT, 0, false>();
+    if (e == cudaSuccess) e = configure_t<DT, 10, true>();
+    if (e == cudaSuccess) e = configure_t<DT, 0, true>();
     return e;
 }
 

@@ -1,8 +1,9 @@
-// Wavefront reconstruction d = M s (Fig. 3 (c)) fused with the leaky integrator
-// a <- leak * a + g * d (Fig. 3 (d)), and the load-time matrix quantisers.
+// Load-time storage of the control matrix in the handle's slice-major layout, and
+// the row-major split-K reconstruction of the allocation-free entry point.
 //
-// The MVM is bound by the bytes of M it streams from HBM (Sec. 1.1.1), so it
-// runs on CUDA cores as a split-K GEMV:
+// Split-K MVM (rtc_mvm_integrate_noalloc, on caller buffers [nact][kpad]): the
+// MVM is bound by the bytes of M it streams from HBM (Sec. 1.1.1), so it runs on
+// CUDA cores as a split-K GEMV:
 //   - block (rb, ks) multiplies rows [4 rb, 4 rb + 4) over the ks-th K slice;
 //     thread t takes the 16-byte chunks t, t+256, ... of the slice for all four
 //     rows, so each s chunk (read through L1) serves four matrix chunks, and the
@@ -34,9 +35,22 @@ __device__ __forceinline__ uint4 ld_stream(const uint4* p) {
     return v;
 }
 
-using rtc_mvm::chunk_dot;
-using rtc_mvm::Epc;
+using rtc_mvm::Esize;
 using rtc_mvm::RowScaled;
+using rtc_mvm::word_dot;
+
+// Elements of the stored type per 16-byte chunk.
+template <int DT> struct Epc { static constexpr int v = 16 / Esize<DT>::v; };
+
+// acc += <16-byte chunk m, its Epc slopes sv>, word by word.
+template <int DT>
+__device__ __forceinline__ float chunk_dot(float acc, const uint4& m, const float* sv) {
+    constexpr int EPW = 4 / Esize<DT>::v;
+    acc = word_dot<DT>(acc, m.x, sv);
+    acc = word_dot<DT>(acc, m.y, sv + EPW);
+    acc = word_dot<DT>(acc, m.z, sv + 2 * EPW);
+    return word_dot<DT>(acc, m.w, sv + 3 * EPW);
+}
 
 template <int DT>
 __device__ __forceinline__ void load_s(const float* __restrict__ s, int chunk, float* sv) {
@@ -159,24 +173,7 @@ mvm_splitk_kernel(const uint4* __restrict__ M, int chunks_per_row, int nact,
     }
 }
 
-// --- load-time quantisers -----------------------------------------------------
-
-__global__ void pad_bf16_kernel(const float* __restrict__ src, int K, int kpad,
-                                __nv_bfloat16* __restrict__ dst) {
-    const int row = blockIdx.x;
-    for (int j = threadIdx.x; j < kpad; j += blockDim.x) {
-        const float v = j < K ? src[static_cast<size_t>(row) * K + j] : 0.f;
-        dst[static_cast<size_t>(row) * kpad + j] = __float2bfloat16_rn(v);
-    }
-}
-
-__global__ void pad_f16_kernel(const float* __restrict__ src, int K, int kpad, __half* __restrict__ dst) {
-    const int row = blockIdx.x;
-    for (int j = threadIdx.x; j < kpad; j += blockDim.x) {
-        const float v = j < K ? src[static_cast<size_t>(row) * K + j] : 0.f;
-        dst[static_cast<size_t>(row) * kpad + j] = __float2half_rn(v);
-    }
-}
+// --- load-time layout ------------------------------------------------------------
 
 // Code of x / sc in the row-scaled formats (one correctly rounded FP32 division).
 template <int DT>
@@ -187,30 +184,56 @@ __device__ __forceinline__ unsigned char encode_scaled(float x, float sc) {
     return static_cast<unsigned char>(static_cast<signed char>(i));
 }
 
-// Per-row scale = max |M_r| / qmax (1 for a zero row) and the row's codes.
+// Per-row scale = max |M_r| / qmax (1 for a zero row), one block per row.
 template <int DT>
-__global__ void quant_rowscaled_kernel(const float* __restrict__ src, int K, int kpad,
-                                       unsigned char* __restrict__ dst, float* __restrict__ scale) {
+__global__ void row_scale_kernel(const float* __restrict__ src, int ncol, float* __restrict__ scale) {
     constexpr float qmax = DT == RTC_FP8_E4M3 ? 448.0f : 127.0f;
     __shared__ float wmax[32];
-    __shared__ float row_scale;
     const int row = blockIdx.x;
-    const float* in = src + static_cast<size_t>(row) * K;
+    const float* in = src + static_cast<size_t>(row) * ncol;
     float m = 0.f;
-    for (int j = threadIdx.x; j < K; j += blockDim.x) m = fmaxf(m, fabsf(in[j]));
+    for (int j = threadIdx.x; j < ncol; j += blockDim.x) m = fmaxf(m, fabsf(in[j]));
     for (int off = 16; off > 0; off >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, off));
     if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = m;
     __syncthreads();
     if (threadIdx.x == 0) {
         float mm = 0.f;
         for (int w = 0; w < static_cast<int>(blockDim.x >> 5); ++w) mm = fmaxf(mm, wmax[w]);
-        row_scale = mm > 0.f ? __fdiv_rn(mm, qmax) : 1.0f;
-        scale[row] = row_scale;
+        scale[row] = mm > 0.f ? __fdiv_rn(mm, qmax) : 1.0f;
     }
-    __syncthreads();
-    const float sc = row_scale;
-    for (int j = threadIdx.x; j < kpad; j += blockDim.x)
-        dst[static_cast<size_t>(row) * kpad + j] = j < K ? encode_scaled<DT>(in[j], sc) : 0;
+}
+
+// One row per block: FP32 column c -> its slice's row in the stored type.
+template <int DT>
+__global__ void layout_f32_kernel(const float* __restrict__ src, int ncol, const int2* __restrict__ colmap,
+                                  const long long* __restrict__ off, const int* __restrict__ rowbytes,
+                                  const float* __restrict__ scale, unsigned char* __restrict__ dst) {
+    const int row = blockIdx.x;
+    const float sc = RowScaled<DT>::v ? scale[row] : 1.f;
+    for (int c = threadIdx.x; c < ncol; c += blockDim.x) {
+        const int2 sj = colmap[c];
+        unsigned char* p = dst + off[sj.x] + static_cast<size_t>(row) * rowbytes[sj.x] +
+                           static_cast<size_t>(sj.y) * Esize<DT>::v;
+        const float v = src[static_cast<size_t>(row) * ncol + c];
+        if (DT == RTC_F32) *reinterpret_cast<float*>(p) = v;
+        else if (DT == RTC_BF16) *reinterpret_cast<__nv_bfloat16*>(p) = __float2bfloat16_rn(v);
+        else if (DT == RTC_F16) *reinterpret_cast<__half*>(p) = __float2half_rn(v);
+        else *p = encode_scaled<DT>(v, sc);
+    }
+}
+
+// One row per block: an element of esize bytes, already in the stored type.
+__global__ void layout_raw_kernel(const unsigned char* __restrict__ src, int ncol, int esize,
+                                  const int2* __restrict__ colmap, const long long* __restrict__ off,
+                                  const int* __restrict__ rowbytes, unsigned char* __restrict__ dst) {
+    const int row = blockIdx.x;
+    for (int c = threadIdx.x; c < ncol; c += blockDim.x) {
+        const int2 sj = colmap[c];
+        unsigned char* p = dst + off[sj.x] + static_cast<size_t>(row) * rowbytes[sj.x] +
+                           static_cast<size_t>(sj.y) * esize;
+        const unsigned char* q = src + (static_cast<size_t>(row) * ncol + c) * esize;
+        for (int b = 0; b < esize; ++b) p[b] = q[b];
+    }
 }
 
 template <int DT>
@@ -250,22 +273,33 @@ cudaError_t launch_mvm_raw(int store, const void* d_M, const float* d_scale, int
     return cudaGetLastError();
 }
 
-cudaError_t launch_quantise(int store, const float* d_src, int nact, int K, int kpad, void* d_dst,
-                            float* d_scale, cudaStream_t st) {
-    if (nact <= 0) return cudaSuccess;
-    unsigned char* q = static_cast<unsigned char*>(d_dst);
+cudaError_t launch_layout(int src, int store, const void* d_src, int nact, int ncol,
+                          const int2* d_colmap, const long long* d_off, const int* d_rowbytes,
+                          float* d_scale, void* d_dst, cudaStream_t st) {
+    if (nact <= 0 || ncol <= 0) return cudaSuccess;
+    unsigned char* dst = static_cast<unsigned char*>(d_dst);
+    if (src == store) {
+        const int esize = store == RTC_F32 ? 4 : (store == RTC_BF16 || store == RTC_F16) ? 2 : 1;
+        layout_raw_kernel<<<nact, 256, 0, st>>>(static_cast<const unsigned char*>(d_src), ncol, esize,
+                                                d_colmap, d_off, d_rowbytes, dst);
+        return cudaGetLastError();
+    }
+    if (src != RTC_F32) return cudaErrorInvalidValue;
+    const float* f = static_cast<const float*>(d_src);
     switch (store) {
         case RTC_BF16:
-            pad_bf16_kernel<<<nact, 256, 0, st>>>(d_src, K, kpad, static_cast<__nv_bfloat16*>(d_dst));
+            layout_f32_kernel<RTC_BF16><<<nact, 256, 0, st>>>(f, ncol, d_colmap, d_off, d_rowbytes, d_scale, dst);
             break;
         case RTC_F16:
-            pad_f16_kernel<<<nact, 256, 0, st>>>(d_src, K, kpad, static_cast<__half*>(d_dst));
+            layout_f32_kernel<RTC_F16><<<nact, 256, 0, st>>>(f, ncol, d_colmap, d_off, d_rowbytes, d_scale, dst);
             break;
         case RTC_FP8_E4M3:
-            quant_rowscaled_kernel<RTC_FP8_E4M3><<<nact, 256, 0, st>>>(d_src, K, kpad, q, d_scale);
+            row_scale_kernel<RTC_FP8_E4M3><<<nact, 256, 0, st>>>(f, ncol, d_scale);
+            layout_f32_kernel<RTC_FP8_E4M3><<<nact, 256, 0, st>>>(f, ncol, d_colmap, d_off, d_rowbytes, d_scale, dst);
             break;
         case RTC_INT8:
-            quant_rowscaled_kernel<RTC_INT8><<<nact, 256, 0, st>>>(d_src, K, kpad, q, d_scale);
+            row_scale_kernel<RTC_INT8><<<nact, 256, 0, st>>>(f, ncol, d_scale);
+            layout_f32_kernel<RTC_INT8><<<nact, 256, 0, st>>>(f, ncol, d_colmap, d_off, d_rowbytes, d_scale, dst);
             break;
         default:
             return cudaErrorInvalidValue;

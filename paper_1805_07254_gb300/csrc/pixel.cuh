@@ -82,9 +82,10 @@ struct NoHook {
 // frame and s_out: this frame's pixels and slope vector (PixelArgs' own fields are
 // not used, so that a persistent kernel can switch buffers per frame cheaply).
 // loaded(): called by every lane after each pass has issued its loads (the
-// passes are the same for every lane, valid or not).
+// passes are the same for every lane, valid or not).  Returns (x, y) slopes on the
+// group's first lane (zeros elsewhere).
 template <int NPX, int LD, int L, typename Hook = NoHook>
-__device__ __forceinline__ void subap_slopes(const PixelArgs& p, const uint16_t* __restrict__ frame,
+__device__ __forceinline__ float2 subap_slopes(const PixelArgs& p, const uint16_t* __restrict__ frame,
                                              float* __restrict__ s_out, int gi, bool valid, int lane,
                                              const Hook& loaded = Hook()) {
     constexpr int kJ = NPX > 0 ? (NPX * NPX + L - 1) / L : kPixPerLane;
@@ -137,15 +138,18 @@ __device__ __forceinline__ void subap_slopes(const PixelArgs& p, const uint16_t*
     comp_group_reduce<L>(F);
     comp_group_reduce<L>(Sx);
     comp_group_reduce<L>(Sy);
+    float2 res = make_float2(0.f, 0.f);
     if (l == 0 && valid) {
         const float f = F.s + F.c;
         const float sx = Sx.s + Sx.c;
         const float sy = Sy.s + Sy.c;
         const bool ok = f > 0.f;
+        res = make_float2(ok ? sx / f : 0.f, ok ? sy / f : 0.f);
         float* s_w = s_out + static_cast<size_t>(w) * 2 * p.n_valid;
-        s_w[i] = ok ? sx / f : 0.f;
-        s_w[p.n_valid + i] = ok ? sy / f : 0.f;
+        s_w[i] = res.x;
+        s_w[p.n_valid + i] = res.y;
     }
+    return res;
 }
 
 }  // namespace rtc_pixel

@@ -68,6 +68,19 @@ void free_predictor(rtc_handle* h) {
     h->pred_on = false;
 }
 
+void free_slices(rtc_handle* h) {
+    free_dev(h->d_sl_off);
+    free_dev(h->d_sl_rowbytes);
+    free_dev(h->d_sl_g0);
+    free_dev(h->d_sl_loc);
+    h->sl_S = 0;
+    h->sl_off.clear();
+    h->sl_rowbytes.clear();
+    h->sl_g0.clear();
+    h->sl_loc.clear();
+    h->m_bytes = 0;
+}
+
 int dtype_size(int dt) {
     switch (dt) {
         case RTC_F32: return 4;
@@ -119,6 +132,7 @@ int apply_subaps(rtc_handle* h, const std::vector<int32_t>& rc) {
     free_dev(h->d_M);
     free_dev(h->d_scale);
     free_dev(h->d_s);
+    free_slices(h);
     h->rc = rc;
     h->n_valid = nv;
     h->nslopes = 2 * nv * h->cfg.n_wfs;
@@ -226,26 +240,24 @@ int rtc_create(const rtc_config* cfg, rtc_handle** out) {
     h->thr = c.thr;
     DeviceScope ds(c.device);
     int rcode = RTC_OK;
-    cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, c.device);
-    if (h->num_sms < 1) h->num_sms = 1;
+    cudaDeviceGetAttribute(&h->dev_sms, cudaDevAttrMultiProcessorCount, c.device);
+    if (h->dev_sms < 1) h->dev_sms = 1;
+    h->num_sms = h->dev_sms;
     if (mvm_stream_configure() != cudaSuccess || frame_kernel_configure() != cudaSuccess ||
         loop_kernel_configure() != cudaSuccess) {
         rcode = fail(nullptr, RTC_EDEVICE, "cannot configure the reconstruction kernel");
     } else if (cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking) != cudaSuccess) {
         rcode = fail(nullptr, RTC_EDEVICE, "cudaStreamCreate failed");
     } else {
-        const size_t nrb = (c.nact + kMvmRows - 1) / kMvmRows;
         const size_t frame_elems = static_cast<size_t>(c.n_wfs) * h->side * h->side;
         if (cudaMalloc(&h->d_a, c.nact * sizeof(float)) != cudaSuccess ||
-            cudaMalloc(&h->d_partial, static_cast<size_t>(kMaxKsplit) * c.nact * sizeof(float)) != cudaSuccess ||
-            cudaMalloc(&h->d_count, nrb * sizeof(unsigned)) != cudaSuccess ||
+            cudaMalloc(&h->d_partial, static_cast<size_t>(h->dev_sms) * c.nact * sizeof(float)) != cudaSuccess ||
             cudaMalloc(&h->d_frame, frame_elems * sizeof(uint16_t)) != cudaSuccess ||
             cudaMalloc(&h->d_status, sizeof(int)) != cudaSuccess ||
             cudaMalloc(&h->d_gridbar, sizeof(unsigned long long)) != cudaSuccess ||
             cudaMallocHost(&h->h_status, sizeof(int)) != cudaSuccess) {
             rcode = fail(nullptr, RTC_ENOMEM, "device allocation failed");
         } else if (cudaMemset(h->d_a, 0, c.nact * sizeof(float)) != cudaSuccess ||
-                   cudaMemset(h->d_count, 0, nrb * sizeof(unsigned)) != cudaSuccess ||
                    cudaMemset(h->d_status, 0, sizeof(int)) != cudaSuccess ||
                    cudaMemset(h->d_gridbar, 0, sizeof(unsigned long long)) != cudaSuccess) {
             rcode = fail(nullptr, RTC_EDEVICE, "cudaMemset failed");
@@ -275,7 +287,7 @@ int rtc_destroy(rtc_handle* h) {
     free_dev(h->d_s);
     free_dev(h->d_a);
     free_dev(h->d_partial);
-    free_dev(h->d_count);
+    free_slices(h);
     free_dev(h->d_frame);
     free_dev(h->d_status);
     free_dev(h->d_gridbar);
@@ -362,36 +374,88 @@ int rtc_load_cmat(rtc_handle* h, const void* M, int32_t nact, int32_t nslopes, i
     RTC_CUDA(h, cudaStreamSynchronize(h->stream));
     free_dev(h->d_M);
     free_dev(h->d_scale);
+    free_slices(h);
     h->store = -1;
-    const int esz = dtype_size(store);
-    const size_t bytes = static_cast<size_t>(nact) * h->kpad * esz;
     RTC_CUDA(h, cudaMalloc(&h->d_scale, nact * sizeof(float)));
-    if (bytes == 0) {            // no valid subapertures: an empty matrix, d = 0
+    if (nslopes == 0) {          // no valid subapertures: an empty matrix, d = 0
         h->store = store;
         return RTC_OK;
     }
-    if (cudaMalloc(&h->d_M, bytes) != cudaSuccess) {
+    // slice table: S slices of consecutive subapertures, each stored as one
+    // contiguous [nact][2 n_s] block (x slopes, then y slopes), rows padded to a
+    // multiple of 4 bytes with an access unit (16, 8 or 4 bytes) that divides them an
+    // odd number of times
+    const int esz = dtype_size(store);
+    const int nt = h->n_valid * h->cfg.n_wfs;
+    const int S = std::min(h->dev_sms, nt);
+    h->sl_S = S;
+    h->sl_g0.resize(S + 1);
+    h->sl_off.resize(S);
+    h->sl_rowbytes.resize(S);
+    h->sl_loc.resize(S + 1);
+    for (int s = 0; s <= S; ++s) h->sl_g0[s] = static_cast<int>(static_cast<long long>(nt) * s / S);
+    long long off = 0;
+    int loc = 0;
+    for (int s = 0; s < S; ++s) {
+        const int n = h->sl_g0[s + 1] - h->sl_g0[s];
+        int rb = (2 * n * esz + 3) / 4 * 4;
+        while (rtc_mvm::row_unit(rb) == 0) rb += 4;       // a bank-conflict-free access unit
+        h->sl_off[s] = off;
+        h->sl_rowbytes[s] = rb;
+        off += (static_cast<long long>(nact) * rb + 15) / 16 * 16;
+        h->sl_loc[s] = loc;
+        loc += (rb / esz + 3) / 4 * 4;
+    }
+    h->sl_loc[S] = loc;
+    h->m_bytes = off;
+    // column c (WFS w, axis, subaperture i) -> (slice, column within the slice)
+    const int nv = h->n_valid;
+    std::vector<int> slice_of(nt);
+    for (int s = 0; s < S; ++s)
+        for (int gi = h->sl_g0[s]; gi < h->sl_g0[s + 1]; ++gi) slice_of[gi] = s;
+    std::vector<int2> colmap(nslopes);
+    for (int c = 0; c < nslopes; ++c) {
+        const int w = c / (2 * nv), rem = c - w * 2 * nv;
+        const int axis = rem >= nv ? 1 : 0;
+        const int gi = w * nv + (rem - axis * nv);
+        const int sl = slice_of[gi];
+        const int n = h->sl_g0[sl + 1] - h->sl_g0[sl];
+        colmap[c] = make_int2(sl, axis * n + (gi - h->sl_g0[sl]));
+    }
+    RTC_CUDA(h, cudaMalloc(&h->d_sl_off, S * sizeof(long long)));
+    RTC_CUDA(h, cudaMalloc(&h->d_sl_rowbytes, S * sizeof(int)));
+    RTC_CUDA(h, cudaMalloc(&h->d_sl_g0, (S + 1) * sizeof(int)));
+    RTC_CUDA(h, cudaMalloc(&h->d_sl_loc, (S + 1) * sizeof(int)));
+    RTC_CUDA(h, cudaMemcpy(h->d_sl_off, h->sl_off.data(), S * sizeof(long long), cudaMemcpyHostToDevice));
+    RTC_CUDA(h, cudaMemcpy(h->d_sl_rowbytes, h->sl_rowbytes.data(), S * sizeof(int), cudaMemcpyHostToDevice));
+    RTC_CUDA(h, cudaMemcpy(h->d_sl_g0, h->sl_g0.data(), (S + 1) * sizeof(int), cudaMemcpyHostToDevice));
+    RTC_CUDA(h, cudaMemcpy(h->d_sl_loc, h->sl_loc.data(), (S + 1) * sizeof(int), cudaMemcpyHostToDevice));
+    if (cudaMalloc(&h->d_M, static_cast<size_t>(h->m_bytes)) != cudaSuccess) {
         h->d_M = nullptr;
-        return fail(h, RTC_ENOMEM, "cannot allocate %zu bytes for the matrix", bytes);
+        free_slices(h);
+        return fail(h, RTC_ENOMEM, "cannot allocate %lld bytes for the matrix", h->m_bytes);
     }
-    RTC_CUDA(h, cudaMemset(h->d_M, 0, bytes));
-    if (src == store) {
-        RTC_CUDA(h, cudaMemcpy2D(h->d_M, static_cast<size_t>(h->kpad) * esz, M,
-                                 static_cast<size_t>(nslopes) * esz, static_cast<size_t>(nslopes) * esz,
-                                 nact, cudaMemcpyHostToDevice));
-        if (scaled)
-            RTC_CUDA(h, cudaMemcpy(h->d_scale, row_scales, nact * sizeof(float), cudaMemcpyHostToDevice));
-    } else {
-        float* staging = nullptr;
-        const size_t sbytes = static_cast<size_t>(nact) * nslopes * sizeof(float);
-        if (cudaMalloc(&staging, sbytes) != cudaSuccess)
-            return fail(h, RTC_ENOMEM, "cannot allocate %zu bytes of staging", sbytes);
-        cudaError_t e = cudaMemcpy(staging, M, sbytes, cudaMemcpyHostToDevice);
-        if (e == cudaSuccess) e = launch_quantise(store, staging, nact, nslopes, h->kpad, h->d_M, h->d_scale, h->stream);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
-        cudaFree(staging);
-        if (e != cudaSuccess) return fail(h, RTC_EDEVICE, "matrix conversion failed: %s", cudaGetErrorString(e));
+    RTC_CUDA(h, cudaMemset(h->d_M, 0, static_cast<size_t>(h->m_bytes)));
+    if (src == store && scaled)
+        RTC_CUDA(h, cudaMemcpy(h->d_scale, row_scales, nact * sizeof(float), cudaMemcpyHostToDevice));
+    // the host matrix through a staging buffer into the slice layout
+    void* staging = nullptr;
+    int2* d_colmap = nullptr;
+    const size_t sbytes = static_cast<size_t>(nact) * nslopes * dtype_size(src);
+    if (cudaMalloc(&staging, sbytes) != cudaSuccess ||
+        cudaMalloc(&d_colmap, nslopes * sizeof(int2)) != cudaSuccess) {
+        if (staging) cudaFree(staging);
+        return fail(h, RTC_ENOMEM, "cannot allocate %zu bytes of staging", sbytes);
     }
+    cudaError_t e = cudaMemcpy(staging, M, sbytes, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(d_colmap, colmap.data(), nslopes * sizeof(int2), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = launch_layout(src, store, staging, nact, nslopes, d_colmap, h->d_sl_off, h->d_sl_rowbytes,
+                          h->d_scale, h->d_M, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    cudaFree(staging);
+    cudaFree(d_colmap);
+    if (e != cudaSuccess) return fail(h, RTC_EDEVICE, "matrix conversion failed: %s", cudaGetErrorString(e));
     h->store = store;
     return RTC_OK;
 }
@@ -476,12 +540,12 @@ int rtc_get_info(const rtc_handle* h, rtc_info* out) {
     out->nact = h->cfg.nact;
     out->kpad = h->kpad;
     out->store = h->store;
-    out->blocks = out->tile_chunks = out->ring_stages = out->reserved = 0;
-    if (h->store >= 0 && h->kpad > 0) {
-        const rtc_mvm::Launch L = rtc_mvm::plan_launch(h, 16 / dtype_size(h->store),
-                                                       h->pred_on ? rtc_pred::kSmemBytes : 0);
+    out->blocks = out->tile_rows = out->ring_stages = 0;
+    out->slices = h->sl_S;
+    if (h->store >= 0 && h->sl_S > 0) {
+        const rtc_mvm::Launch L = rtc_mvm::plan_launch(h, h->pred_on ? rtc_pred::kSmemBytes : 0);
         out->blocks = L.G;
-        out->tile_chunks = L.tw;
+        out->tile_rows = L.R;
         out->ring_stages = L.nst;
     }
     const int64_t entries = static_cast<int64_t>(h->cfg.nact) * h->nslopes;
@@ -520,10 +584,10 @@ bool rtc_handle_ready(const rtc_handle* h) { return h && h->calib_loaded && h->s
 int64_t rtc_handle_device_bytes(const rtc_handle* h) {
     const int64_t nact = h->cfg.nact, kpad = h->kpad, nw = h->cfg.n_wfs;
     const int64_t npp = static_cast<int64_t>(h->cfg.npx) * h->cfg.npx;
-    int64_t b = nact * kpad * std::max(dtype_size(h->store), 1) + 4 * nact;   // matrix + scales
+    int64_t b = h->m_bytes + 4 * nact;                                         // matrix + scales
     b += 2 * 4 * nw * h->n_valid * npp;                                        // dark + gain
     b += nw * static_cast<int64_t>(h->side) * h->side * 2;                     // frame staging
-    b += 4 * (kpad + nact) + 4 * static_cast<int64_t>(kMaxKsplit) * nact + 4 * nact;  // s, a, partials
+    b += 4 * (kpad + nact) + 4 * static_cast<int64_t>(h->dev_sms) * nact + 4 * nact;  // s, a, partials
     if (h->pred) b += 4 * (5 * kpad) + 4 * 25 * h->n_valid + 3 * 4 * RTC_MLP_NPARAMS + 2 * (64 * 208 + 64 * 64);
     return b;
 }

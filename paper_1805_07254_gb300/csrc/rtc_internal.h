@@ -49,7 +49,8 @@ struct rtc_handle {
     bool calib_loaded = false;
 
     cudaStream_t stream = nullptr;
-    int num_sms = 1;                // streaming multiprocessors of the device
+    int num_sms = 1;                // blocks the fused kernels may use (a server slot lowers it)
+    int dev_sms = 1;                // streaming multiprocessors of the device
 
     std::vector<int32_t> rc;    // host copy of the subaperture map (row, col) pairs
 
@@ -57,12 +58,22 @@ struct rtc_handle {
     int2* d_rc = nullptr;           // [n_valid] (row, col) grid position of each valid subap
     float* d_dark = nullptr;        // [n_wfs][n_valid][npx*npx] dark, subap-major
     float* d_gainmap = nullptr;     // [n_wfs][n_valid][npx*npx] 1/flat, subap-major
-    void* d_M = nullptr;            // [nact][kpad] in the stored type
-    float* d_scale = nullptr;       // [nact] FP8 row scales
+    void* d_M = nullptr;            // slice-major matrix in the stored type (see stream_mvm.cuh)
+    int64_t m_bytes = 0;            // bytes of d_M
+    float* d_scale = nullptr;       // [nact] FP8 / INT8 row scales
+    // slice table of the loaded matrix: S slices of consecutive subapertures
+    int sl_S = 0;
+    std::vector<long long> sl_off;  // [S] byte offset of each slice (16-byte aligned)
+    std::vector<int> sl_rowbytes;   // [S] bytes per row (multiple of 4)
+    std::vector<int> sl_g0;         // [S + 1] first subaperture of each slice
+    std::vector<int> sl_loc;        // [S + 1] float offset of each slice's slopes in a local vector
+    long long* d_sl_off = nullptr;
+    int* d_sl_rowbytes = nullptr;
+    int* d_sl_g0 = nullptr;
+    int* d_sl_loc = nullptr;
     float* d_s = nullptr;           // [kpad] slope vector, zero padded
     float* d_a = nullptr;           // [nact] integrator state
-    float* d_partial = nullptr;     // [kMaxKsplit][nact] split-K partial products (scratch)
-    unsigned* d_count = nullptr;    // [ceil(nact/kMvmRows)] arrival counters (scratch, self-resetting)
+    float* d_partial = nullptr;     // [dev_sms][nact] partial DM vectors, one per slice (scratch)
     uint16_t* d_frame = nullptr;    // [n_wfs][side][side] staging for host frames
     int* d_status = nullptr;        // device-side error word (RTC_ETIMEDOUT from bounded waits)
     unsigned long long* d_gridbar = nullptr;  // grid-barrier arrival counter (only grows)
@@ -98,9 +109,8 @@ struct rtc_handle {
 cudaError_t launch_calib_cog(const rtc_handle* h, const uint16_t* d_frame, float* d_s,
                              cudaStream_t st);
 
-// Streaming MVM (persistent, TMA bulk copies) with the fixed-order partial tree and
-// the leaky integrator; d_partial holds shared-row-group partials, d_count their
-// self-resetting arrival counters.
+// Slice-by-slice reconstruction (TMA bulk copies) with the fixed-order sum of the
+// partial DM vectors and the leaky integrator (see stream_mvm.cuh).
 cudaError_t mvm_stream_configure();
 cudaError_t launch_decay(const rtc_handle* h, float* d_dm_out, cudaStream_t st);
 
@@ -116,7 +126,7 @@ cudaError_t launch_loop(rtc_handle* h, const LoopLaunch& ll, cudaStream_t st);
 // `head` of h->d_ring, predicted slopes into h->d_spred, reconstruction from those.
 cudaError_t launch_frame(rtc_handle* h, const uint16_t* d_frame, float* d_dm_out, float* d_s_meas,
                          int head, cudaStream_t st);
-cudaError_t launch_mvm_integrate(const rtc_handle* h, const float* d_s, float* d_dm_out,
+cudaError_t launch_mvm_integrate(rtc_handle* h, const float* d_s, float* d_dm_out,
                                  cudaStream_t st);
 
 // The same split-K MVM + integrator on caller-described buffers: matrix [nact][kpad]
@@ -126,9 +136,13 @@ cudaError_t launch_mvm_raw(int store, const void* d_M, const float* d_scale, int
                            const float* d_s, int ksplit, float* d_partial, unsigned* d_count,
                            float* d_a, float* d_dm_out, float gain, float leak, cudaStream_t st);
 
-// Convert an FP32 device matrix [nact][K] into the stored layout [nact][kpad].
-cudaError_t launch_quantise(int store, const float* d_src, int nact, int K, int kpad,
-                            void* d_dst, float* d_scale, cudaStream_t st);
+// Store a device matrix [nact][ncol] (FP32, or already in the stored type when
+// src == store) into the slice-major layout: column c goes to slice colmap[c].x,
+// local column colmap[c].y.  From FP32, the FP8 / INT8 row scales are computed
+// into d_scale first.
+cudaError_t launch_layout(int src, int store, const void* d_src, int nact, int ncol,
+                          const int2* d_colmap, const long long* d_off, const int* d_rowbytes,
+                          float* d_scale, void* d_dst, cudaStream_t st);
 
 // Read and clear the device status word after `st` drains (RTC_OK or the recorded
 // error, which also restarts the grid-barrier count); set the handle's message.

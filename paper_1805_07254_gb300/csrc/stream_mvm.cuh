@@ -1,43 +1,38 @@
-// Device code of the streaming reconstruction d = M s fused with the leaky
-// integrator a <- leak * a + g * d (Fig. 3 (c)-(d)), shared by the stand-alone
-// reconstruction kernel, the fused frame kernel and the persistent loop kernel.
+// Device code of the reconstruction d = M s fused with the leaky integrator
+// a <- leak * a + g * d (Fig. 3 (c)-(d)), shared by the stand-alone reconstruction
+// kernel, the fused frame kernel and the persistent loop kernel.
 //
-// The MVM is the path's bandwidth-bound bulk (Sec. 1.1.1: every frame streams the
-// whole control matrix from memory), so it runs on CUDA cores as a GEMV.
+// Decomposition (Sec. 2.3, 2.3.5).  As in the paper, where each thread takes a set
+// of subapertures, multiplies the matrix columns of their slopes and leaves a
+// partial DM vector that a tree then sums, the slope columns are cut into S slices
+// of consecutive subapertures (S = the SM count, or the number of subapertures if
+// smaller).  rtc_load_cmat stores the matrix slice by slice: slice s is one
+// contiguous [nact][w_s] block, its w_s = 2 n_s columns being the slice's x slopes
+// then its y slopes, each row padded to a multiple of 4 bytes.  A block of a fused
+// kernel takes a run of whole slices and computes those subapertures' slopes
+// itself, so its share of the product starts as soon as its own pixels are done,
+// without waiting for any other block; it writes one partial vector per slice.
+// After one grid barrier every block sums the S partials of its share of the rows
+// in a fixed order (warp w sums the slices w, w+14, w+28, ... in turn for 32
+// consecutive rows with coalesced loads, then a fixed pairwise tree over the 14
+// warps), applies the FP8/INT8 row scale and the integrator.
+// The result does not depend on the number of blocks or on their timing.
 //
-// Work.  The matrix is [nact][kpad] row-major in its stored type; rows are taken
-// four at a time ("row groups") so that each slope chunk serves four matrix
-// chunks.  The (row group, 16-byte column chunk) units are cut into G equal
-// contiguous ranges, one per block (one block per SM), so every SM streams the
-// same number of bytes.  A block's range is a list of jobs: row groups it owns
-// whole, plus at most a head (leading chunks) and a tail (trailing chunks) of a
-// row group it shares with a neighbour.
-//
-// Movement.  Tiles of 4 row segments x tw chunks are copied into shared memory
-// with bulk asynchronous copies (TMA, `cp.async.bulk`) that complete on per-stage
-// mbarriers.  tw splits a row into the fewest equal tiles of at most 448 chunks
-// (28 KB per tile), so a row gives no small remainder tile, and the rings take as
-// many stages (up to 8 per team) as shared memory holds: short reduced-precision
-// rows get deeper rings, so the bytes in flight per SM, which hide the HBM
-// latency, stay at 150-190 KB for every stored type.  Two teams of 7 consumer
-// warps take alternate jobs; each team has its own ring, its own producer thread
-// and its own full/empty barriers, and consumes its ring in order (a ring shared
-// by teams that consume out of order would let a wait on a later phase pass
-// early).  One team's reduction overlaps the other's tiles.  Each consumer thread
-// takes two chunks per row of a tile and issues all of its shared-memory loads
-// before its FMAs.  (Deferring the reductions to the end of a block's work, so
-// that a team's warps never meet between row groups, measured slower: the tail
-// grows.)  The slope vector is copied once per block into shared memory
-// (bank-swizzled) when it fits in 64 KB, else read through L1/L2.
+// Movement.  A slice streams in tiles of R rows, bulk asynchronous copies
+// (`cp.async.bulk`) completing on a per-stage mbarrier, through a ring of up to 8
+// stages in shared memory that one producer thread fills and 14 consumer warps
+// drain.  T consecutive lanes take one row of a tile (T = 1 for ELT-sized slices,
+// more when rows are long, so that at least two stages fit) and read it in units of
+// 16, 8 or 4 bytes, the widest that divides the row an odd number of times (rows
+// are padded until one does), so that the rows a warp reads at once fall in
+// different banks; all lanes read the same units of the slice's slopes at the same
+// time (shared-memory broadcasts).
 //
 // Arithmetic.  Stored values are widened to FP32 just before the FMA (BF16 by a
 // shift, FP16 by the half2 -> float2 conversion, E4M3 by the hardware fp8x2 ->
-// f16x2 conversion, INT8 exactly through the mantissa of 2^23; the FP8 and INT8
-// row scales are applied once after the sum), as Sec. 2.3.4 widens its 16-bit
-// matrix.  Partial sums are combined in a fixed order -- xor butterfly in each
-// warp, pairwise tree over the team's 7 warps, and for a shared row group head +
-// tail, added by whichever of the two blocks finishes second -- the GPU form of
-// the partial-DM-vector tree of Sec. 2.3.5.  Results do not depend on scheduling.
+// f16x2 conversion, INT8 exactly through the mantissa of 2^23), as Sec. 2.3.4
+// widens its 16-bit matrix; the FP8 and INT8 row scales are applied once per row
+// after the sum over slices.
 //
 // Every wait is bounded (200 ms of %globaltimer); a wait that expires records
 // RTC_ETIMEDOUT in the status word, the block skips the rest of its work, lets its
@@ -47,32 +42,30 @@
 #include <cuda_fp16.h>
 #include <cuda_fp8.h>
 
+#include <algorithm>
+
 #include "rtc_internal.h"
 
 namespace rtc_mvm {
 
-constexpr int kTeams = 2;                          // consumer teams, taking alternate row groups
-constexpr int kTeamWarps = 7;                      // 2 x 7 consumer + 1 producer warp: 15 warps,
-                                                   // so 128 registers per thread are available
-constexpr int kTeamThreads = kTeamWarps * 32;
-constexpr int kConsumerWarps = kTeams * kTeamWarps;
+constexpr int kConsumerWarps = 14;
 constexpr int kConsumers = kConsumerWarps * 32;
-constexpr int kThreads = kConsumers + 32;          // + one producer warp (lane t feeds team t)
-constexpr int kRows = kMvmRows;                    // rows per row group
-constexpr int kU = 2;                              // chunks per consumer thread per row per tile
-constexpr int kCH = kTeamThreads * kU;             // most 16-byte chunks per row segment per tile
-constexpr int kMaxTeamStages = 8;                  // stages per team ring (2..8 at run time)
+constexpr int kThreads = kConsumers + 32;          // + one producer warp
+constexpr int kMaxStages = 8;
 constexpr unsigned long long kWaitNs = 200ull * 1000 * 1000;
-constexpr int kMaxPrefetchBytes = 16 * 1024;       // integrator state + scales of a block's rows
-constexpr int kMaxSBytes = 64 * 1024;              // slope vector kept in shared memory up to this
+constexpr int kMaxLocalFloats = 8192;              // slopes of a block's slices (32 KB)
+constexpr int kMaxRowFloats = 4096;                // rows a block reduces, at most
 constexpr size_t kDynSmemBudget = 227 * 1024 - 2048;  // dynamic shared memory per block
+constexpr int kMaxSlices = 256;
+constexpr int kSlicesPerWarp = (kMaxSlices + kConsumerWarps - 1) / kConsumerWarps;
+constexpr uint32_t kCopyBytes = 8192;              // largest single bulk copy of a tile
 
-template <int DT> struct Epc;
-template <> struct Epc<RTC_F32> { static constexpr int v = 4; };
-template <> struct Epc<RTC_BF16> { static constexpr int v = 8; };
-template <> struct Epc<RTC_F16> { static constexpr int v = 8; };
-template <> struct Epc<RTC_FP8_E4M3> { static constexpr int v = 16; };
-template <> struct Epc<RTC_INT8> { static constexpr int v = 16; };
+template <int DT> struct Esize;
+template <> struct Esize<RTC_F32> { static constexpr int v = 4; };
+template <> struct Esize<RTC_BF16> { static constexpr int v = 2; };
+template <> struct Esize<RTC_F16> { static constexpr int v = 2; };
+template <> struct Esize<RTC_FP8_E4M3> { static constexpr int v = 1; };
+template <> struct Esize<RTC_INT8> { static constexpr int v = 1; };
 
 // Stored types whose rows carry one FP32 scale, applied once after the row's sum.
 template <int DT> struct RowScaled { static constexpr bool v = DT == RTC_FP8_E4M3 || DT == RTC_INT8; };
@@ -114,6 +107,16 @@ __device__ __forceinline__ unsigned long long global_ns() {
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
     return t;
 }
+__device__ __forceinline__ uint32_t lds32(uint32_t addr) {
+    uint32_t v;
+    asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(addr));
+    return v;
+}
+__device__ __forceinline__ uint2 lds64(uint32_t addr) {
+    uint2 v;
+    asm volatile("ld.shared.v2.u32 {%0,%1}, [%2];" : "=r"(v.x), "=r"(v.y) : "r"(addr));
+    return v;
+}
 __device__ __forceinline__ uint4 lds128(uint32_t addr) {
     uint4 v;
     asm volatile("ld.shared.v4.u32 {%0,%1,%2,%3}, [%4];"
@@ -121,16 +124,18 @@ __device__ __forceinline__ uint4 lds128(uint32_t addr) {
                  : "r"(addr));
     return v;
 }
-__device__ __forceinline__ void sts128(uint32_t addr, const float4& v) {
-    asm volatile("st.shared.v4.f32 [%0], {%1,%2,%3,%4};" ::"r"(addr), "f"(v.x), "f"(v.y), "f"(v.z),
-                 "f"(v.w)
-                 : "memory");
+
+// Access unit of a slice row of rb bytes: the widest of 16, 8, 4 bytes that divides
+// the row an odd number of times, so that the rows a warp reads at once (rb bytes
+// apart) fall in different banks.  rtc_load_cmat pads rows until one exists.
+__host__ __device__ __forceinline__ int row_unit(int rb) {
+    if (rb % 16 == 0 && (rb / 16) % 2 == 1) return 16;
+    if (rb % 8 == 0 && (rb / 8) % 2 == 1) return 8;
+    if (rb % 4 == 0 && (rb / 4) % 2 == 1) return 4;
+    return 0;
 }
 __device__ __forceinline__ void consumer_sync() {          // all consumer warps
     asm volatile("bar.sync 1, %0;" ::"n"(kConsumers) : "memory");
-}
-__device__ __forceinline__ void team_sync(int team) {      // the 8 warps of one team
-    asm volatile("bar.sync %0, %1;" ::"r"(2 + team), "n"(kTeamThreads) : "memory");
 }
 
 // Bounded wait on an mbarrier phase; false if it expired or (when abort is given)
@@ -145,15 +150,18 @@ __device__ __forceinline__ bool wait_phase(uint32_t bar, uint32_t parity, volati
     }
 }
 
-// Bank swizzle of the shared slope copy: piece j (16 bytes) of chunk c sits in
-// slot j ^ swz(c), so the pieces the lanes of a warp read together fall in
-// different banks although their chunks are E*4 bytes apart.
-template <int E>
-__device__ __forceinline__ int s_swizzle(int chunk) {
-    return E == 16 ? ((chunk >> 1) & 3) : E == 8 ? ((chunk >> 2) & 1) : 0;
+// Bounded wait for a shared-memory flag; false if it expired or the block aborted.
+__device__ __forceinline__ bool wait_flag(volatile int* flag, volatile int* abort) {
+    const unsigned long long t0 = global_ns();
+    while (!*flag) {
+        if (*abort) return false;
+        if (global_ns() - t0 > kWaitNs) return false;
+        __nanosleep(64);
+    }
+    return true;
 }
 
-// ---- widening dot products (acc += <16-byte chunk, s values>) ------------------
+// ---- widening dot products: acc += <one 4-byte word of a row, its slopes> -------
 __device__ __forceinline__ float2 e4m3x2_to_float2(uint32_t two) {
     __half2_raw hr = __nv_cvt_fp8x2_to_halfraw2(static_cast<__nv_fp8x2_storage_t>(two), __NV_E4M3);
     return __half22float2(*reinterpret_cast<__half2*>(&hr));
@@ -165,45 +173,36 @@ __device__ __forceinline__ float i8_to_float(uint32_t flipped, int k) {
     return __uint_as_float(__byte_perm(flipped, 0x4B000000u, 0x7650 + k)) - 8388736.0f;
 }
 
+// acc += <word w, its EPW slopes s>.  (Placing FP8 / FP16 bits at the top of an FP32
+// mantissa and pre-scaling the slopes by 2^120 / 2^112 avoids the conversion
+// instructions but measured slower than the hardware conversions.)
 template <int DT>
-__device__ __forceinline__ float chunk_dot(float acc, const uint4& m, const float* sv) {
-    const uint32_t w[4] = {m.x, m.y, m.z, m.w};
+__device__ __forceinline__ float word_dot(float acc, uint32_t w, const float* s) {
     if (DT == RTC_F32) {
-#pragma unroll
-        for (int j = 0; j < 4; ++j) acc = fmaf(__uint_as_float(w[j]), sv[j], acc);
+        acc = fmaf(__uint_as_float(w), s[0], acc);
     } else if (DT == RTC_BF16) {
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            acc = fmaf(__uint_as_float(w[j] << 16), sv[2 * j], acc);
-            acc = fmaf(__uint_as_float(w[j] & 0xffff0000u), sv[2 * j + 1], acc);
-        }
+        acc = fmaf(__uint_as_float(w << 16), s[0], acc);
+        acc = fmaf(__uint_as_float(w & 0xffff0000u), s[1], acc);
     } else if (DT == RTC_F16) {
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            __half2_raw hr;
-            hr.x = static_cast<unsigned short>(w[j] & 0xffffu);
-            hr.y = static_cast<unsigned short>(w[j] >> 16);
-            const float2 f = __half22float2(*reinterpret_cast<__half2*>(&hr));
-            acc = fmaf(f.x, sv[2 * j], acc);
-            acc = fmaf(f.y, sv[2 * j + 1], acc);
-        }
-    } else if (DT == RTC_INT8) {
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const uint32_t x = w[j] ^ 0x80808080u;
-#pragma unroll
-            for (int k = 0; k < 4; ++k) acc = fmaf(i8_to_float(x, k), sv[4 * j + k], acc);
-        }
+        __half2_raw hr;
+        hr.x = static_cast<unsigned short>(w & 0xffffu);
+        hr.y = static_cast<unsigned short>(w >> 16);
+        const float2 f = __half22float2(*reinterpret_cast<__half2*>(&hr));
+        acc = fmaf(f.x, s[0], acc);
+        acc = fmaf(f.y, s[1], acc);
+    } else if (DT == RTC_FP8_E4M3) {
+        const float2 a = e4m3x2_to_float2(w & 0xffffu);
+        const float2 b = e4m3x2_to_float2(w >> 16);
+        acc = fmaf(a.x, s[0], acc);
+        acc = fmaf(a.y, s[1], acc);
+        acc = fmaf(b.x, s[2], acc);
+        acc = fmaf(b.y, s[3], acc);
     } else {
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const float2 a = e4m3x2_to_float2(w[j] & 0xffffu);
-            const float2 b = e4m3x2_to_float2(w[j] >> 16);
-            acc = fmaf(a.x, sv[4 * j + 0], acc);
-            acc = fmaf(a.y, sv[4 * j + 1], acc);
-            acc = fmaf(b.x, sv[4 * j + 2], acc);
-            acc = fmaf(b.y, sv[4 * j + 3], acc);
-        }
+        const uint32_t x = w ^ 0x80808080u;
+        acc = fmaf(i8_to_float(x, 0), s[0], acc);
+        acc = fmaf(i8_to_float(x, 1), s[1], acc);
+        acc = fmaf(i8_to_float(x, 2), s[2], acc);
+        acc = fmaf(i8_to_float(x, 3), s[3], acc);
     }
     return acc;
 }
@@ -219,317 +218,306 @@ __device__ __forceinline__ void integrate_row(int row, float d, float a_prev, fl
     if (dm_out) dm_out[row] = an;
 }
 
+// ---- plan ----------------------------------------------------------------------
+
+// The slice table of a loaded matrix (device arrays).
+struct Slices {
+    const long long* off;    // [S] byte offset of slice s in the matrix (16-byte aligned)
+    const int* rowbytes;     // [S] bytes per row of slice s (multiple of 4)
+    const int* g0;           // [S + 1] first subaperture (w * n_valid + i) of slice s
+    const int* loc;          // [S + 1] float offset of slice s's slopes in a local vector
+    int S;
+};
+
 struct Args {
-    const unsigned char* M;  // [nact][cpr * 16 bytes]
-    int cpr, nact, nst;      // chunks per row, rows, stages per team ring
-    int tw, stage_bytes;     // tile width in chunks (<= kCH), bytes of one stage (kRows * tw * 16)
-    const float* s;          // [cpr * E] slopes, zero padded
+    const unsigned char* M;  // slice-major matrix
+    Slices sl;
+    int nact, n_valid;       // rows; valid subapertures per WFS
+    int T, R;                // lanes per row, rows per tile (T * R = kConsumers)
+    int stage_bytes, nst;    // bytes per ring stage, stages
+    int region;              // shared scratch bytes of a fused phase (before the slopes)
+    int loc_floats;          // floats of the largest block-local slope vector
+    int row_floats;          // rows a block reduces, at most
+    const float* s;          // stand-alone reconstruction: the full slope vector (else unused)
     const float* scale;      // [nact] row scales (FP8, INT8)
-    float* slots;            // [nrg][2][4] partials of shared row groups (scratch)
-    unsigned* counters;      // [nrg] arrival counters (scratch, self-resetting)
+    float* partial;          // [S][nact] partial DM vectors
     float* a;                // [nact] integrator state
     float* dm_out;           // [nact] or nullptr
     float gain, leak;
     int* status;             // device error word
-    int region;              // bytes of shared memory between the rings and the prefetch
-                             // area: the slope copy, or a fused phase's scratch before it
 };
 
 struct Shared {
-    unsigned long long full_bar[kTeams][kMaxTeamStages];
-    unsigned long long empty_bar[kTeams][kMaxTeamStages];
-    float red[kTeams][kRows][kTeamWarps];
+    unsigned long long full_bar[kMaxStages];
+    unsigned long long empty_bar[kMaxStages];
     volatile int abort_flag;
-    volatile int release;    // set once the slopes are known (see produce's hold)
+    volatile int release;    // set once the block's slopes are known (see produce's hold)
 };
 
-// What one block does, from its share of the (row group, chunk) space.
+// What one block does.
 struct Plan {
-    long long u0, u1;        // [u0, u1) units, row-group major
-    int rg_first, rg_last;
-    int row_lo, nrow_blk;    // rows touched by the block
-    uint32_t smem_base;      // stage rings (kTeams * nst * stage_bytes)
-    uint32_t s_smem;         // slope copy (S_SMEM)
-    unsigned char* scratch;  // the same region, free until consumer_prologue
-    float* a_pre;            // [nrow_blk] integrator state of the block's rows
-    float* sc_pre;           // [nrow_blk] row scales of the block's rows
+    int sb0, sb1;            // slices [sb0, sb1)
+    int g0, g1;              // subapertures [g0, g1)
+    int r0, r1;              // rows the block reduces
+    uint32_t ring;           // shared address of the ring
+    unsigned char* scratch;  // fused-phase scratch (region bytes)
+    float* loc;              // block-local slopes: each slice's x then y block, zero padded
+    float* a_pre;            // [r1 - r0] integrator state of the rows the block reduces
+    float* sc_pre;           // [r1 - r0] their row scales
+    float* red;              // [kConsumerWarps][32] warp sums of the sum over slices
 };
 
 __device__ __forceinline__ void init_shared(Shared& sh) {
-    for (int t = 0; t < kTeams; ++t)
-        for (int i = 0; i < kMaxTeamStages; ++i) {
-            mbar_init(smem_addr(&sh.full_bar[t][i]), 1);
-            mbar_init(smem_addr(&sh.empty_bar[t][i]), kTeamWarps);
-        }
+    for (int i = 0; i < kMaxStages; ++i) {
+        mbar_init(smem_addr(&sh.full_bar[i]), 1);
+        mbar_init(smem_addr(&sh.empty_bar[i]), kConsumerWarps);
+    }
     sh.abort_flag = 0;
     sh.release = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
 
-template <int DT, bool S_SMEM>
 __device__ __forceinline__ Plan make_plan(const Args& g, unsigned char* smem) {
     Plan pl;
-    const int nrg = (g.nact + kRows - 1) / kRows;
-    const long long total = static_cast<long long>(nrg) * g.cpr;
-    pl.u0 = total * blockIdx.x / gridDim.x;
-    pl.u1 = total * (blockIdx.x + 1) / gridDim.x;
-    pl.rg_first = static_cast<int>(pl.u0 / g.cpr);
-    pl.rg_last = static_cast<int>((pl.u1 - 1) / g.cpr);
-    pl.row_lo = pl.rg_first * kRows;
-    pl.nrow_blk = min(g.nact, (pl.rg_last + 1) * kRows) - pl.row_lo;
-    pl.smem_base = smem_addr(smem);
-    const int ring_bytes = kTeams * g.nst * g.stage_bytes;
-    pl.s_smem = pl.smem_base + ring_bytes;
+    const int S = g.sl.S;
+    pl.sb0 = static_cast<int>(static_cast<long long>(S) * blockIdx.x / gridDim.x);
+    pl.sb1 = static_cast<int>(static_cast<long long>(S) * (blockIdx.x + 1) / gridDim.x);
+    pl.g0 = g.sl.g0[pl.sb0];
+    pl.g1 = g.sl.g0[pl.sb1];
+    pl.r0 = static_cast<int>(static_cast<long long>(g.nact) * blockIdx.x / gridDim.x);
+    pl.r1 = static_cast<int>(static_cast<long long>(g.nact) * (blockIdx.x + 1) / gridDim.x);
+    const int ring_bytes = g.nst * g.stage_bytes;
+    pl.ring = smem_addr(smem);
     pl.scratch = smem + ring_bytes;
-    pl.a_pre = reinterpret_cast<float*>(smem + ring_bytes + g.region);
-    pl.sc_pre = pl.a_pre + pl.nrow_blk;
+    pl.loc = reinterpret_cast<float*>(smem + ring_bytes + g.region);
+    pl.a_pre = pl.loc + g.loc_floats;
+    pl.sc_pre = pl.a_pre + g.row_floats;
+    pl.red = pl.sc_pre + g.row_floats;
     return pl;
 }
 
-__device__ __forceinline__ void job_bounds(const Args& g, const Plan& pl, int rg, int& kb, int& ke) {
-    kb = (rg == pl.rg_first) ? static_cast<int>(pl.u0 % g.cpr) : 0;
-    ke = (rg == pl.rg_last) ? static_cast<int>((pl.u1 - 1) % g.cpr) + 1 : g.cpr;
+// Where subaperture gi (one of the block's) puts its x and y slopes in the
+// block-local vector.
+__device__ __forceinline__ void local_index(const Args& g, const Plan& pl, int gi, int& ix, int& iy) {
+    int s = pl.sb0;
+    while (s + 1 < pl.sb1 && g.sl.g0[s + 1] <= gi) ++s;
+    const int base = g.sl.loc[s] - g.sl.loc[pl.sb0];
+    const int n = g.sl.g0[s + 1] - g.sl.g0[s];
+    ix = base + (gi - g.sl.g0[s]);
+    iy = ix + n;
 }
 
-// Bounded wait for a shared-memory flag; false if it expired or the block aborted.
-__device__ __forceinline__ bool wait_flag(volatile int* flag, volatile int* abort) {
-    const unsigned long long t0 = global_ns();
-    while (!*flag) {
-        if (*abort) return false;
-        if (global_ns() - t0 > kWaitNs) return false;
-        __nanosleep(64);
+// Consumers: clear the block-local slope vector (its padding stays zero).
+__device__ __forceinline__ void clear_local(const Args& g, const Plan& pl, int tid) {
+    for (int i = tid; i < g.loc_floats; i += kConsumers) pl.loc[i] = 0.f;
+}
+
+// Consumers: the block's slopes from a full slope vector s (x block then y block per
+// WFS).  fresh: s was written by other blocks of the same kernel (read from L2).
+__device__ __forceinline__ void gather_local(const Args& g, const Plan& pl, int tid,
+                                             const float* __restrict__ s, bool fresh) {
+    for (int gi = pl.g0 + tid; gi < pl.g1; gi += kConsumers) {
+        const int w = gi / g.n_valid, i = gi - w * g.n_valid;
+        const size_t bx = static_cast<size_t>(w) * 2 * g.n_valid + i;
+        int ix, iy;
+        local_index(g, pl, gi, ix, iy);
+        pl.loc[ix] = fresh ? __ldcg(s + bx) : __ldg(s + bx);
+        pl.loc[iy] = fresh ? __ldcg(s + bx + g.n_valid) : __ldg(s + bx + g.n_valid);
     }
-    return true;
 }
 
-// One team's producer (a single thread): stream the team's jobs into its ring.
-// tl0: the team's running tile count at entry (barrier phases continue across
-// calls, e.g. frame after frame in a persistent kernel); returns the count at exit.
-// drain: wait for the last copies to land before returning (a block must not exit
-// with copies in flight).  hold > 0: after the first `hold` tiles, wait until the
-// consumers set sh.release (the latency-critical pixel stage and grid barrier
-// then run in a memory system that is not flooded by the matrix stream).
-__device__ __forceinline__ int produce(const Args& g, const Plan& pl, Shared& sh, int team,
-                                       int tl0 = 0, bool drain = true, int hold = 0) {
-    const size_t pitch = static_cast<size_t>(g.cpr) * 16;
-    const uint32_t ring = pl.smem_base + team * g.nst * g.stage_bytes;
+// Consumers: integrator state and row scales of the rows the block reduces.
+template <int DT>
+__device__ __forceinline__ void prefetch_rows(const Args& g, const Plan& pl, int tid) {
+    for (int r = pl.r0 + tid; r < pl.r1; r += kConsumers) {
+        pl.a_pre[r - pl.r0] = __ldcg(g.a + r);
+        pl.sc_pre[r - pl.r0] = RowScaled<DT>::v ? g.scale[r] : 1.f;
+    }
+}
+
+// One producer thread: stream the block's slices tile by tile into the ring.
+// tl0: the running tile count at entry (barrier phases continue across calls, e.g.
+// frame after frame in a persistent kernel); returns the count at exit.  drain: wait
+// for the last copies to land before returning (a block must not exit with copies
+// in flight).  hold > 0: after the first `hold` tiles, wait until the consumers set
+// sh.release (the latency-critical pixel loads then do not queue behind the stream).
+__device__ __forceinline__ int produce(const Args& g, const Plan& pl, Shared& sh, int tl0 = 0,
+                                       bool drain = true, int hold = 0) {
     int tl = tl0;
     bool ok = true;
-    for (int rg = pl.rg_first + team; rg <= pl.rg_last && ok; rg += kTeams) {
-        int kb, ke;
-        job_bounds(g, pl, rg, kb, ke);
-        const int nrows = min(kRows, g.nact - rg * kRows);
-        for (int k = kb; k < ke; k += g.tw, ++tl) {
+    for (int s = pl.sb0; s < pl.sb1 && ok; ++s) {
+        const unsigned char* base = g.M + g.sl.off[s];
+        const int rb = g.sl.rowbytes[s];
+        for (int row0 = 0; row0 < g.nact; row0 += g.R, ++tl) {
             if (hold > 0 && tl - tl0 == hold && !wait_flag(&sh.release, &sh.abort_flag)) {
                 ok = false;
                 break;
             }
             const int st = tl % g.nst;
             const int use = tl / g.nst;
-            if (use > 0 &&
-                !wait_phase(smem_addr(&sh.empty_bar[team][st]), (use - 1) & 1, &sh.abort_flag)) {
+            if (use > 0 && !wait_phase(smem_addr(&sh.empty_bar[st]), (use - 1) & 1, &sh.abort_flag)) {
                 ok = false;
                 break;
             }
-            const int nck = min(g.tw, ke - k);
-            const uint32_t bytes = static_cast<uint32_t>(nck) * 16;
-            const uint32_t fb = smem_addr(&sh.full_bar[team][st]);
-            mbar_expect_tx(fb, bytes * nrows);
-            for (int r = 0; r < nrows; ++r) {
-                const unsigned char* src = g.M + static_cast<size_t>(rg * kRows + r) * pitch +
-                                           static_cast<size_t>(k) * 16;
-                bulk_g2s(ring + st * g.stage_bytes + r * g.tw * 16, src, bytes, fb);
-            }
+            const int rows = min(g.R, g.nact - row0);
+            // the slice is padded to 16 bytes, so the last tile may round up; the tile
+            // goes as several copies
+            const uint32_t bytes = (static_cast<uint32_t>(rows) * rb + 15u) & ~15u;
+            const uint32_t fb = smem_addr(&sh.full_bar[st]);
+            mbar_expect_tx(fb, bytes);
+            const unsigned char* src = base + static_cast<size_t>(row0) * rb;
+            for (uint32_t o = 0; o < bytes; o += kCopyBytes)
+                bulk_g2s(pl.ring + st * g.stage_bytes + o, src + o, min(kCopyBytes, bytes - o), fb);
         }
     }
     if (!ok && !sh.abort_flag) {
         atomicExch(g.status, RTC_ETIMEDOUT);
         sh.abort_flag = 1;
     }
-    // let every issued copy land before the block can exit
     if (drain || !ok)
         for (int t = max(tl0, tl - g.nst); t < tl; ++t)
-            wait_phase(smem_addr(&sh.full_bar[team][t % g.nst]), (t / g.nst) & 1, nullptr);
+            wait_phase(smem_addr(&sh.full_bar[t % g.nst]), (t / g.nst) & 1, nullptr);
     return tl;
 }
 
-// Consumers, before their first tile: integrator state and scales of the block's
-// rows into shared memory (a demand miss at the end of every row group would queue
-// behind the matrix stream), and the slope copy.  FRESH: read s from L2 (it was
-// written by other blocks of the same kernel).  Ends with a consumer barrier.
-template <int DT, bool S_SMEM, bool FRESH>
-__device__ __forceinline__ void consumer_prologue(const Args& g, const Plan& pl, int tid,
-                                                  const float* __restrict__ s_vec) {
-    constexpr int E = Epc<DT>::v;
-    for (int i = tid; i < pl.nrow_blk; i += kConsumers) {
-        pl.a_pre[i] = FRESH ? __ldcg(g.a + pl.row_lo + i) : g.a[pl.row_lo + i];
-        pl.sc_pre[i] = RowScaled<DT>::v ? g.scale[pl.row_lo + i] : 1.f;
-    }
-    if (S_SMEM) {
-        // up to kBatch loads in flight per thread before the first store: the copy
-        // costs about one L2 round trip, not one per piece
-        constexpr int P = E / 4;
-        constexpr int kBatch = 4;
-        const int npieces = g.cpr * P;
-        for (int p0 = tid; p0 < npieces; p0 += kBatch * kConsumers) {
-            float4 v[kBatch];
+// The EPU slopes of one unit into registers with vector loads (shared-memory
+// broadcasts: every lane of the warp reads the same unit at the same time).
+template <int EPU>
+__device__ __forceinline__ void load_unit(const float* s, float* r) {
+    if (EPU % 4 == 0) {
 #pragma unroll
-            for (int b = 0; b < kBatch; ++b) {
-                const int p = p0 + b * kConsumers;
-                if (p < npieces) {
-                    const float4* src = reinterpret_cast<const float4*>(s_vec) + p;
-                    v[b] = FRESH ? __ldcg(src) : __ldg(src);
-                }
-            }
-#pragma unroll
-            for (int b = 0; b < kBatch; ++b) {
-                const int p = p0 + b * kConsumers;
-                if (p < npieces) {
-                    const int c = p / P;
-                    const int j = p - c * P;
-                    sts128(pl.s_smem + static_cast<uint32_t>(c * P + (j ^ s_swizzle<E>(c))) * 16, v[b]);
-                }
-            }
+        for (int j = 0; j < EPU; j += 4) {
+            const float4 v = *reinterpret_cast<const float4*>(s + j);
+            r[j] = v.x;
+            r[j + 1] = v.y;
+            r[j + 2] = v.z;
+            r[j + 3] = v.w;
         }
+    } else if (EPU == 2) {
+        const float2 v = *reinterpret_cast<const float2*>(s);
+        r[0] = v.x;
+        r[1] = v.y;
+    } else {
+        r[0] = s[0];
     }
-    consumer_sync();
 }
 
-// The consumer teams: multiply every tile of the team's jobs and finalise each
-// row group (integrator, or the shared head/tail exchange).
-// tile0: the team's running tile count at entry; returns the count at exit.
-// s_vec: the slope vector; dm_out: where the new commands go besides g.a (or null).
-template <int DT, bool S_SMEM, bool FRESH>
-__device__ __forceinline__ int consume(const Args& g, const Plan& pl, Shared& sh, int tid,
-                                       int tile0, const float* __restrict__ s_vec,
-                                       float* __restrict__ dm_out) {
-    constexpr int E = Epc<DT>::v;
-    const int warp = tid >> 5;
-    const int lane = tid & 31;
-    const int team = warp / kTeamWarps;
-    const int twarp = warp - team * kTeamWarps;
-    const int ttid = tid - team * kTeamThreads;
-    const uint32_t ring = pl.smem_base + team * g.nst * g.stage_bytes;
-    int tile = tile0;                                                // team-local tile index
-    for (int rg = pl.rg_first + team; rg <= pl.rg_last; rg += kTeams) {
-        int kb, ke;
-        job_bounds(g, pl, rg, kb, ke);
-        const int nrows = min(kRows, g.nact - rg * kRows);
-        float acc[kU][kRows];
-#pragma unroll
-        for (int u = 0; u < kU; ++u)
-#pragma unroll
-            for (int r = 0; r < kRows; ++r) acc[u][r] = 0.f;
-        for (int k = kb; k < ke; k += g.tw, ++tile) {
-            const int st = tile % g.nst;
-            const bool ok = __all_sync(0xffffffffu, wait_phase(smem_addr(&sh.full_bar[team][st]),
-                                                                (tile / g.nst) & 1, &sh.abort_flag));
-            if (!ok) {
-                if (lane == 0 && !sh.abort_flag) {
-                    atomicExch(g.status, RTC_ETIMEDOUT);
-                    sh.abort_flag = 1;
-                }
-                continue;     // skip the work but keep reaching the block's barriers
-            }
-            const int nck = min(g.tw, ke - k);
-            // issue every shared-memory load of this tile before any FMA; rows past
-            // nact hold stale bytes and their sums are never used
-            uint4 m[kU][kRows];
-            float sv[kU][E];
-#pragma unroll
-            for (int u = 0; u < kU; ++u) {
-                const int c = ttid + u * kTeamThreads;
-                if (c < nck) {
-                    if (S_SMEM) {
-                        const uint32_t sp = pl.s_smem + static_cast<uint32_t>(k + c) * (E * 4);
-                        const int sw = s_swizzle<E>(k + c);
-#pragma unroll
-                        for (int j = 0; j < E / 4; ++j) {
-                            const uint4 v = lds128(sp + ((j ^ sw) * 16));
-                            sv[u][4 * j] = __uint_as_float(v.x);
-                            sv[u][4 * j + 1] = __uint_as_float(v.y);
-                            sv[u][4 * j + 2] = __uint_as_float(v.z);
-                            sv[u][4 * j + 3] = __uint_as_float(v.w);
-                        }
-                    } else {
-                        const float4* sp =
-                            reinterpret_cast<const float4*>(s_vec) + static_cast<size_t>(k + c) * (E / 4);
-#pragma unroll
-                        for (int j = 0; j < E / 4; ++j) {
-                            const float4 v = FRESH ? __ldcg(sp + j) : __ldg(sp + j);
-                            sv[u][4 * j] = v.x;
-                            sv[u][4 * j + 1] = v.y;
-                            sv[u][4 * j + 2] = v.z;
-                            sv[u][4 * j + 3] = v.w;
-                        }
-                    }
-                    const uint32_t sb = ring + st * g.stage_bytes + c * 16;
-#pragma unroll
-                    for (int r = 0; r < kRows; ++r) m[u][r] = lds128(sb + r * g.tw * 16);
-                }
-            }
-#pragma unroll
-            for (int u = 0; u < kU; ++u)
-                if (ttid + u * kTeamThreads < nck)
-#pragma unroll
-                    for (int r = 0; r < kRows; ++r) acc[u][r] = chunk_dot<DT>(acc[u][r], m[u][r], sv[u]);
-            __syncwarp();
-            if (lane == 0) mbar_arrive(smem_addr(&sh.empty_bar[team][st]));
+// Dot product of one slice row (in shared memory at rbase, nunits units of U bytes,
+// lane part of T lanes taking units part, part + T, ...) with the slice's slopes sv.
+template <int DT, int U>
+__device__ __forceinline__ float row_dot(uint32_t rbase, const float* sv, int nunits, int part, int T) {
+    constexpr int EPW = 4 / Esize<DT>::v;                    // elements per 4-byte word
+    constexpr int EPU = U / Esize<DT>::v;                    // elements per unit
+    float acc = 0.f;
+#pragma unroll 4
+    for (int k = part; k < nunits; k += T) {
+        float r[EPU];
+        load_unit<EPU>(sv + k * EPU, r);
+        if (U == 16) {
+            const uint4 m = lds128(rbase + 16 * k);
+            acc = word_dot<DT>(acc, m.x, r);
+            acc = word_dot<DT>(acc, m.y, r + EPW);
+            acc = word_dot<DT>(acc, m.z, r + 2 * EPW);
+            acc = word_dot<DT>(acc, m.w, r + 3 * EPW);
+        } else if (U == 8) {
+            const uint2 m = lds64(rbase + 8 * k);
+            acc = word_dot<DT>(acc, m.x, r);
+            acc = word_dot<DT>(acc, m.y, r + EPW);
+        } else {
+            acc = word_dot<DT>(acc, lds32(rbase + 4 * k), r);
         }
+    }
+    return acc;
+}
 
-        // fixed-order reduction of the row group's 4 partial sums over the team
-#pragma unroll
-        for (int r = 0; r < kRows; ++r) {
-            float v = acc[0][r];
-#pragma unroll
-            for (int u = 1; u < kU; ++u) v += acc[u][r];
-#pragma unroll
-            for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-            if (lane == 0) sh.red[team][r][twarp] = v;
-        }
-        team_sync(team);
-        if (twarp == 0 && !sh.abort_flag) {
-            float d = 0.f;
-            if (lane < kRows) {
-                float v[kTeamWarps];
-#pragma unroll
-                for (int w = 0; w < kTeamWarps; ++w) v[w] = sh.red[team][lane][w];
-#pragma unroll
-                for (int width = 1; width < kTeamWarps; width <<= 1)
-#pragma unroll
-                    for (int i = 0; i + width < kTeamWarps; i += 2 * width) v[i] += v[i + width];
-                d = v[0];
+// The tiles of one slice; returns the running tile count.
+template <int DT, int U>
+__device__ __forceinline__ int consume_slice(const Args& g, const Plan& pl, Shared& sh, int tid,
+                                             int tile, int s) {
+    const int lane = tid & 31;
+    const int rt = tid / g.T;                                // row of the tile
+    const int part = tid - rt * g.T;                         // lane within the row's group
+    const int rb = g.sl.rowbytes[s];
+    const int nunits = rb / U;
+    const float* sv = pl.loc + (g.sl.loc[s] - g.sl.loc[pl.sb0]);
+    float* out = g.partial + static_cast<size_t>(s) * g.nact;
+    for (int row0 = 0; row0 < g.nact; row0 += g.R, ++tile) {
+        const int st = tile % g.nst;
+        const bool ok = __all_sync(0xffffffffu, wait_phase(smem_addr(&sh.full_bar[st]),
+                                                            (tile / g.nst) & 1, &sh.abort_flag));
+        if (!ok) {
+            if (lane == 0 && !sh.abort_flag) {
+                atomicExch(g.status, RTC_ETIMEDOUT);
+                sh.abort_flag = 1;
             }
-            const int row = rg * kRows + lane;
-            if (kb == 0 && ke == g.cpr) {
-                if (lane < nrows)
-                    integrate_row<DT>(row, d, pl.a_pre[row - pl.row_lo], pl.sc_pre[row - pl.row_lo],
-                                      g.a, dm_out, g.gain, g.leak);
-            } else {
-                // shared row group: head (kb == 0) -> slot 0, tail -> slot 1
-                const int part = (kb == 0) ? 0 : 1;
-                if (lane < kRows) g.slots[(static_cast<size_t>(rg) * 2 + part) * kRows + lane] = d;
-                __threadfence();
-                __syncwarp();
-                unsigned prev = 0;
-                if (lane == 0) prev = atomicAdd(g.counters + rg, 1u);
-                prev = __shfl_sync(0xffffffffu, prev, 0);
-                if (prev == 1) {
-                    __threadfence();
-                    if (lane < nrows) {
-                        const float h = __ldcg(g.slots + (static_cast<size_t>(rg) * 2 + 0) * kRows + lane);
-                        const float t = __ldcg(g.slots + (static_cast<size_t>(rg) * 2 + 1) * kRows + lane);
-                        integrate_row<DT>(row, h + t, __ldcg(g.a + row),
-                                          RowScaled<DT>::v ? g.scale[row] : 1.f, g.a, dm_out,
-                                          g.gain, g.leak);
-                    }
-                    if (lane == 0) g.counters[rg] = 0u;
-                }
-            }
+            continue;     // skip the work but keep reaching the block's barriers
         }
-        team_sync(team);
+        const int row = row0 + rt;
+        float acc = 0.f;
+        if (row < g.nact)
+            acc = row_dot<DT, U>(pl.ring + st * g.stage_bytes + rt * rb, sv, nunits, part, g.T);
+        for (int off = g.T >> 1; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+        if (part == 0 && row < g.nact) out[row] = acc;
+        __syncwarp();
+        if (lane == 0) mbar_arrive(smem_addr(&sh.empty_bar[st]));
     }
     return tile;
+}
+
+// The consumer warps: every tile of the block's slices, one partial vector per
+// slice (partial[s][row] = the row's dot product with the slice's slopes, in unit
+// order).  tile0: the running tile count at entry; returns the count at exit.
+template <int DT>
+__device__ __forceinline__ int consume(const Args& g, const Plan& pl, Shared& sh, int tid, int tile0) {
+    int tile = tile0;
+    for (int s = pl.sb0; s < pl.sb1; ++s) {
+        const int u = row_unit(g.sl.rowbytes[s]);
+        if (u == 16) tile = consume_slice<DT, 16>(g, pl, sh, tid, tile, s);
+        else if (u == 8) tile = consume_slice<DT, 8>(g, pl, sh, tid, tile, s);
+        else tile = consume_slice<DT, 4>(g, pl, sh, tid, tile, s);
+    }
+    return tile;
+}
+
+// After the grid barrier that follows every block's partials: the rows [r0, r1) of
+// the block, 32 at a time (one per lane), each summed over the S slices in a fixed
+// order -- warp w adds the slices w, w+14, w+28, ... in turn (coalesced loads of 32
+// consecutive rows of one slice), then warp 0 adds the 14 warp sums in a pairwise
+// tree -- then the row scale and the integrator.  dm_out: where the new commands go
+// besides g.a.
+template <int DT>
+__device__ __forceinline__ void reduce_rows(const Args& g, const Plan& pl, int tid,
+                                            float* __restrict__ dm_out) {
+    const int warp = tid >> 5, lane = tid & 31;
+    for (int base = pl.r0; base < pl.r1; base += 32) {
+        const int row = base + lane;
+        float v = 0.f;
+        if (row < pl.r1) {
+            float p[kSlicesPerWarp];
+#pragma unroll
+            for (int j = 0; j < kSlicesPerWarp; ++j) {
+                const int s = warp + j * kConsumerWarps;
+                p[j] = s < g.sl.S ? __ldcg(g.partial + static_cast<size_t>(s) * g.nact + row) : 0.f;
+            }
+#pragma unroll
+            for (int j = 0; j < kSlicesPerWarp; ++j)
+                if (warp + j * kConsumerWarps < g.sl.S) v += p[j];
+        }
+        pl.red[warp * 32 + lane] = v;
+        consumer_sync();
+        if (warp == 0 && row < pl.r1) {
+            float t[kConsumerWarps];
+#pragma unroll
+            for (int w = 0; w < kConsumerWarps; ++w) t[w] = pl.red[w * 32 + lane];
+#pragma unroll
+            for (int width = 1; width < kConsumerWarps; width <<= 1)
+#pragma unroll
+                for (int i = 0; i + width < kConsumerWarps; i += 2 * width) t[i] += t[i + width];
+            integrate_row<DT>(row, t[0], pl.a_pre[row - pl.r0], pl.sc_pre[row - pl.r0], g.a, dm_out,
+                              g.gain, g.leak);
+        }
+        consumer_sync();
+    }
 }
 
 // Grid barrier over co-resident blocks: one thread per block, after a block-level
@@ -555,46 +543,70 @@ __device__ __forceinline__ bool grid_barrier(unsigned long long* bar, unsigned l
     return true;
 }
 
-// Grid, stages per team ring and dynamic shared memory of a launch for one handle.
+// Grid, tiles, stages and dynamic shared memory of a launch for one handle.
 struct Launch {
-    int G, nst;
-    int tw, stage_bytes;     // tile width (chunks) and stage size
-    size_t smem;
-    size_t region;           // slope copy / fused-phase scratch bytes
-    bool s_in_smem;
+    int G, T, R, nst, stage_bytes, loc_floats, row_floats;
+    size_t smem, region;
     bool ok;
 };
 
-// min_region: shared-memory scratch a fused phase needs before the reconstruction.
-inline Launch plan_launch(const rtc_handle* h, int elems_per_chunk, size_t min_region = 0) {
+// min_region: shared-memory scratch a fused phase needs.  Uses the handle's slice
+// table, built when the matrix was loaded.
+inline Launch plan_launch(const rtc_handle* h, size_t min_region = 0) {
     Launch L{};
-    const int nrg = (h->cfg.nact + kRows - 1) / kRows;
-    L.G = nrg < h->num_sms ? nrg : h->num_sms;
-    const size_t pre = static_cast<size_t>((nrg + L.G - 1) / L.G + 2) * kRows * 2 * sizeof(float);
-    const size_t s_bytes = static_cast<size_t>(h->kpad) * sizeof(float);
-    L.s_in_smem = s_bytes <= static_cast<size_t>(kMaxSBytes);
-    L.region = L.s_in_smem ? s_bytes : 0;
-    if (L.region < min_region) L.region = (min_region + 15) / 16 * 16;
-    const size_t extra = L.region + pre;
-    // a row splits into the fewest equal tiles of at most kCH chunks (no small
-    // remainder tile), and the rings take as many stages as fit
-    const int cpr = elems_per_chunk > 0 ? h->kpad / elems_per_chunk : 0;
-    const int ntile = cpr > 0 ? (cpr + kCH - 1) / kCH : 1;
-    L.tw = cpr > 0 ? (cpr + ntile - 1) / ntile : kCH;
+    const int S = h->sl_S;
+    L.G = S < h->num_sms ? S : h->num_sms;
+    if (L.G < 1 || S < 1 || static_cast<int>(h->sl_rowbytes.size()) != S) return L;
+    // largest row and largest block-local slope vector over the blocks
+    int max_rb = 0, max_loc = 0;
+    for (int b = 0; b < L.G; ++b) {
+        const int s0 = static_cast<int>(static_cast<long long>(S) * b / L.G);
+        const int s1 = static_cast<int>(static_cast<long long>(S) * (b + 1) / L.G);
+        max_loc = std::max(max_loc, h->sl_loc[s1] - h->sl_loc[s0]);
+        for (int s = s0; s < s1; ++s) max_rb = std::max(max_rb, h->sl_rowbytes[s]);
+    }
+    L.loc_floats = (max_loc + 3) / 4 * 4;
+    L.row_floats = (h->cfg.nact + L.G - 1) / L.G;
+    L.region = (min_region + 15) / 16 * 16;
+    const size_t extra = L.region + 4 * static_cast<size_t>(L.loc_floats) +
+                         8 * static_cast<size_t>(L.row_floats) + 4 * kConsumerWarps * 32;
     const size_t room = kDynSmemBudget > extra ? kDynSmemBudget - extra : 0;
-    L.stage_bytes = kRows * L.tw * 16;
-    const size_t fit = room / (static_cast<size_t>(kTeams) * L.stage_bytes);
-    L.nst = static_cast<int>(fit < static_cast<size_t>(kMaxTeamStages) ? fit : kMaxTeamStages);
-    L.smem = static_cast<size_t>(kTeams) * L.nst * L.stage_bytes + extra;
-    L.ok = L.nst >= 2 && pre <= static_cast<size_t>(kMaxPrefetchBytes) && L.smem <= kDynSmemBudget &&
-           h->kpad % (16 * 4 / 4) == 0 && elems_per_chunk > 0;
+    // fewest lanes per row for which two stages of R = kConsumers / T rows fit
+    auto stage = [&](int T) { return (static_cast<size_t>(kConsumers / T) * max_rb + 15) / 16 * 16; };
+    L.T = 1;
+    while (L.T < 16 && 2 * stage(L.T) > room) L.T *= 2;      // R stays a multiple of 4
+    L.R = kConsumers / L.T;
+    L.stage_bytes = static_cast<int>(stage(L.T));
+    const size_t fit = L.stage_bytes > 0 ? room / L.stage_bytes : 0;
+    L.nst = static_cast<int>(fit < static_cast<size_t>(kMaxStages) ? fit : kMaxStages);
+    L.smem = static_cast<size_t>(L.nst) * L.stage_bytes + extra;
+    L.ok = L.nst >= 2 && L.loc_floats <= kMaxLocalFloats && L.row_floats <= kMaxRowFloats &&
+           S <= kMaxSlices && L.smem <= kDynSmemBudget;
     return L;
 }
 
-inline Args make_args(const rtc_handle* h, const float* d_s, float* d_dm_out, const Launch& L, int epc) {
-    return Args{static_cast<const unsigned char*>(h->d_M), h->kpad / epc, h->cfg.nact, L.nst,
-                L.tw, L.stage_bytes, d_s, h->d_scale, h->d_partial, h->d_count, h->d_a, d_dm_out,
-                h->gain, h->leak, h->d_status, static_cast<int>(L.region)};
+inline Args make_args(const rtc_handle* h, const float* d_s, float* d_dm_out, const Launch& L) {
+    Args g{};
+    g.M = static_cast<const unsigned char*>(h->d_M);
+    g.sl = Slices{h->d_sl_off, h->d_sl_rowbytes, h->d_sl_g0, h->d_sl_loc, h->sl_S};
+    g.nact = h->cfg.nact;
+    g.n_valid = h->n_valid;
+    g.T = L.T;
+    g.R = L.R;
+    g.stage_bytes = L.stage_bytes;
+    g.nst = L.nst;
+    g.region = static_cast<int>(L.region);
+    g.loc_floats = L.loc_floats;
+    g.row_floats = L.row_floats;
+    g.s = d_s;
+    g.scale = h->d_scale;
+    g.partial = h->d_partial;
+    g.a = h->d_a;
+    g.dm_out = d_dm_out;
+    g.gain = h->gain;
+    g.leak = h->leak;
+    g.status = h->d_status;
+    return g;
 }
 
 }  // namespace rtc_mvm

@@ -30,8 +30,8 @@ class RtcConfig(C.Structure):
 
 class RtcInfo(C.Structure):
     _fields_ = [("n_valid", C.c_int32), ("nslopes", C.c_int32), ("nact", C.c_int32),
-                ("kpad", C.c_int32), ("store", C.c_int32), ("blocks", C.c_int32),
-                ("tile_chunks", C.c_int32), ("ring_stages", C.c_int32), ("reserved", C.c_int32),
+                ("kpad", C.c_int32), ("store", C.c_int32), ("slices", C.c_int32),
+                ("blocks", C.c_int32), ("tile_rows", C.c_int32), ("ring_stages", C.c_int32),
                 ("matrix_bytes", C.c_int64), ("frame_bytes", C.c_int64), ("calib_bytes", C.c_int64)]
 
 

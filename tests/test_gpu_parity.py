@@ -49,24 +49,41 @@ def test_tiny_scao_closed_loop_1000_frames():
 
 
 @pytest.mark.parametrize("store", ["f32", "bf16", "f16", "fp8", "int8"])
-def test_launch_plan_streams_equal_tiles(store):
-    """One block per SM (at most one per row group); rows split into equal tiles of
-    at most 448 chunks; rings of 2..8 stages; the plan covers every row chunk."""
+def test_launch_plan_slices_and_tiles(store):
+    """One slice of consecutive subapertures per SM (fewer if there are fewer
+    subapertures), one block per slice, tiles of 448 / T rows, rings of 2..8 stages;
+    short reduced-precision rows get deeper rings than FP32 rows."""
     cfg = synth.elt_scao()
     r, *_ = make_pair(cfg, store=store)
     info = r.info()
     sms = torch.cuda.get_device_properties(0).multi_processor_count
-    assert info["blocks"] == min(sms, (cfg.nact + 3) // 4)
-    epc = {"f32": 4, "bf16": 8, "f16": 8, "fp8": 16, "int8": 16}[store]
-    cpr = info["kpad"] // epc
-    tw = info["tile_chunks"]
-    ntile = -(-cpr // tw)
-    assert 0 < tw <= 448 and ntile == -(-cpr // 448) and tw * ntile - cpr < ntile
+    assert info["slices"] == min(sms, cfg.n_valid)
+    assert info["blocks"] == info["slices"]
+    assert info["tile_rows"] in (448, 224, 112, 56, 28)
     assert 2 <= info["ring_stages"] <= 8
-    # a short row gets a deeper ring than a long one
     if store in ("fp8", "int8"):
         r32, *_ = make_pair(cfg, store="f32")
         assert info["ring_stages"] > r32.info()["ring_stages"]
+    tiny, *_ = make_pair(synth.tiny_scao(), store=store)
+    assert tiny.info()["slices"] == min(sms, synth.tiny_scao().n_valid)
+
+
+@pytest.mark.parametrize("store", ["f32", "fp8"])
+def test_results_do_not_depend_on_the_block_count(store):
+    """The partial DM vectors are per slice and summed in a fixed order, so a handle
+    limited to a quarter of the SMs (a server slot) gives the standalone results bit
+    for bit."""
+    from paper_1805_07254_gb300 import Server
+    cfg = synth.elt_scao()
+    frames, _ = synth.make_frames(cfg, 0, 4)
+    frames = frames.numpy()
+    r1, *_ = make_pair(cfg, store=store)
+    r2, *_ = make_pair(cfg, store=store)
+    ref = np.stack([r1.process_frame(frames[k]) for k in range(4)])
+    srv = Server(max_slots=4)
+    slot = srv.submit(r2, frames)
+    dm = srv.wait(slot)
+    np.testing.assert_array_equal(dm, ref)
 
 
 @pytest.mark.parametrize("mode,thr", [(0, 5.0), (1, 5.0), (0, -1e9), (1, 40.0)])
