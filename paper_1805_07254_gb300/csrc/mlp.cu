@@ -112,7 +112,8 @@ struct Smem {
     static constexpr int TGT = DY + TM * NO * 4;                    // f32 [TM][NO]
     static constexpr int RED = TGT + TM * NO * 4;                   // f32 [NH] scratch sums
     static constexpr int LOSS = RED + NH * 4 * 2;                   // f32 [kWarps]
-    static constexpr int TOTAL = LOSS + 64;
+    static constexpr int SAMP = (LOSS + 64 + 15) / 16 * 16;         // int2 [TM] (subap, frame)
+    static constexpr int TOTAL = SAMP + TM * 8;
 };
 
 // Weights into shared memory: BF16 copies of W1 (padded), W2 and W2^T; FP32 rest.
@@ -124,18 +125,78 @@ __device__ void load_weights(unsigned char* sm, const MlpDev& w) {
     float* b2 = reinterpret_cast<float*>(sm + Smem::B2);
     float* W3 = reinterpret_cast<float*>(sm + Smem::W3);
     float* b3 = reinterpret_cast<float*>(sm + Smem::B3);
-    for (int i = threadIdx.x; i < NH * KP; i += kThreads) W1[i] = w.w1_bf16[i];
-    for (int i = threadIdx.x; i < NH * NH; i += kThreads) {
-        W2[i] = w.w2_bf16[i];
-        const int n = i / NH, k = i - n * NH;
-        W2T[i] = w.w2_bf16[k * NH + n];
-    }
+    // 16-byte copies of the BF16 weights, then W2^T from the shared copy
+    for (int i = threadIdx.x; i < NH * KP / 8; i += kThreads)
+        reinterpret_cast<uint4*>(W1)[i] = __ldg(reinterpret_cast<const uint4*>(w.w1_bf16) + i);
+    for (int i = threadIdx.x; i < NH * NH / 8; i += kThreads)
+        reinterpret_cast<uint4*>(W2)[i] = __ldg(reinterpret_cast<const uint4*>(w.w2_bf16) + i);
     for (int i = threadIdx.x; i < NH; i += kThreads) {
         b1[i] = w.master[OFF_B1 + i];
         b2[i] = w.master[OFF_B2 + i];
     }
     for (int i = threadIdx.x; i < NO * NH; i += kThreads) W3[i] = w.master[OFF_W3 + i];
     if (threadIdx.x < NO) b3[threadIdx.x] = w.master[OFF_B3 + threadIdx.x];
+    __syncthreads();
+    for (int i = threadIdx.x; i < NH * NH; i += kThreads) {
+        const int n = i / NH, k = i - n * NH;
+        W2T[i] = W2[k * NH + n];
+    }
+}
+
+// Features of the CTA's samples from slope rows, by (sample, neighbour) pairs: for a
+// batch of pairs every neighbour index is loaded at once, then every slope value of
+// the batch, before the stores (the gather is latency-bound).  X[s][f] and, if
+// want_t, XT[f][s] get bf16(value / sigma) with f = (lag*2 + axis)*25 + nb; off-pupil
+// neighbours and invalid samples give 0.  subap_of(s): the sample's subaperture or
+// -1; row_of(s, lag): its slope row at that lag (x block then y block).
+template <typename SubFn, typename RowFn>
+__device__ void gather_pairs(unsigned char* sm, bool want_t, const int* __restrict__ nbr, int nv,
+                             float inv_sigma, const SubFn& subap_of, const RowFn& row_of) {
+    bf16* X = reinterpret_cast<bf16*>(sm + Smem::X);
+    bf16* XT = reinterpret_cast<bf16*>(sm + Smem::XT);
+    constexpr int kPairs = TM * 25;
+    constexpr int kBatch = 5;
+    for (int p0 = threadIdx.x; p0 < kPairs; p0 += kBatch * kThreads) {
+        int j[kBatch];
+#pragma unroll
+        for (int b = 0; b < kBatch; ++b) {
+            const int p = p0 + b * kThreads;
+            j[b] = -1;
+            if (p < kPairs) {
+                const int si = p / 25;
+                const int i = subap_of(si);
+                if (i >= 0) j[b] = __ldg(nbr + i * 25 + (p - si * 25));
+            }
+        }
+        float v[kBatch][8];
+#pragma unroll
+        for (int b = 0; b < kBatch; ++b) {
+            const int si = (p0 + b * kThreads) / 25;
+#pragma unroll
+            for (int la = 0; la < 8; ++la)
+                v[b][la] = j[b] >= 0 ? row_of(si, la >> 1)[(la & 1) * nv + j[b]] : 0.f;
+        }
+#pragma unroll
+        for (int b = 0; b < kBatch; ++b) {
+            const int p = p0 + b * kThreads;
+            if (p < kPairs) {
+                const int si = p / 25, nb = p - si * 25;
+#pragma unroll
+                for (int la = 0; la < 8; ++la) {
+                    const int f = la * 25 + nb;
+                    const bf16 x = __float2bfloat16_rn(v[b][la] * inv_sigma);
+                    X[si * KP + f] = x;
+                    if (want_t) XT[f * TM + si] = x;
+                }
+            }
+        }
+    }
+    // the K padding columns
+    for (int q = threadIdx.x; q < TM * (KP - NF); q += kThreads) {
+        const int si = q / (KP - NF), c = NF + (q - si * (KP - NF));
+        X[si * KP + c] = __float2bfloat16_rn(0.f);
+        if (want_t) XT[c * TM + si] = __float2bfloat16_rn(0.f);
+    }
 }
 
 // Feature rows of the CTA's samples: x[s][f] for s < ns (zero rows beyond), as BF16
@@ -367,19 +428,6 @@ __global__ void __launch_bounds__(kThreads) mlp_forward_kernel(MlpDev w, const f
     for (int i = threadIdx.x; i < ns * NO; i += kThreads) Yout[static_cast<size_t>(s0) * NO + i] = Y[i];
 }
 
-// Feature of subaperture i from 4 slope rows (newest first), 5x5 neighbour table.
-struct HistFeat {
-    const float* rows[4];
-    const int* nbr;          // [nv][25]: neighbour index or -1
-    int nv, i;
-    float inv_sigma;
-    __device__ float operator()(int f) const {
-        const int dc = f % 5, dr = (f / 5) % 5, axis = (f / 25) & 1, lag = f / 50;
-        const int j = nbr[i * 25 + dr * 5 + dc];
-        return j >= 0 ? rows[lag][axis * nv + j] * inv_sigma : 0.f;
-    }
-};
-
 // Training samples from a slope sequence S [nframes][2 nv]: sample (i, k) uses frames
 // k..k-3 as features and (S[k+1] - S[k]) / sigma of subaperture i as the target.
 __global__ void __launch_bounds__(kThreads) mlp_train_seq_kernel(MlpDev w, const float* __restrict__ S,
@@ -394,17 +442,14 @@ __global__ void __launch_bounds__(kThreads) mlp_train_seq_kernel(MlpDev w, const
     const size_t row = 2 * static_cast<size_t>(nv);
     // a sample outside the sequence or the pupil contributes zero features and target
     auto valid = [&](int2 sk) { return sk.x >= 0 && sk.x < nv && sk.y >= 3 && sk.y <= n_frames - 2; };
-    gather_tile(sm, ns, true, [&](int s, int f) {
-        const int2 sk = samples[s0 + s];           // (subaperture, frame k)
-        if (!valid(sk)) return 0.f;
-        HistFeat hf;
-        for (int lag = 0; lag < 4; ++lag) hf.rows[lag] = S + (sk.y - lag) * row;
-        hf.nbr = nbr;
-        hf.nv = nv;
-        hf.i = sk.x;
-        hf.inv_sigma = inv_sigma;
-        return hf(f);
-    });
+    int2* samp = reinterpret_cast<int2*>(sm + Smem::SAMP);
+    for (int si = threadIdx.x; si < TM; si += kThreads) {
+        const int2 sk = si < ns ? samples[s0 + si] : make_int2(-1, 0);
+        samp[si] = valid(sk) ? sk : make_int2(-1, 0);
+    }
+    __syncthreads();
+    gather_pairs(sm, true, nbr, nv, inv_sigma, [&](int si) { return samp[si].x; },
+                 [&](int si, int lag) { return S + static_cast<size_t>(samp[si].y - lag) * row; });
     float* TG = reinterpret_cast<float*>(sm + Smem::TGT);
     for (int q = threadIdx.x; q < TM * NO; q += kThreads) {
         const int s = q / NO, o = q - s * NO;
@@ -431,23 +476,17 @@ __global__ void __launch_bounds__(kThreads) mlp_predict_kernel(MlpDev w, const f
     const int s0 = blockIdx.x * TM;
     const int ns = min(TM, nv - s0);
     load_weights(sm, w);
-    HistFeat hf;
-    for (int lag = 0; lag < 4; ++lag) hf.rows[lag] = ring + static_cast<size_t>((head - lag + 4) & 3) * kpad;
-    hf.nbr = nbr;
-    hf.nv = nv;
-    hf.inv_sigma = 1.f / sigma;
-    gather_tile(sm, ns, false, [&](int s, int f) {
-        HistFeat h = hf;
-        h.i = s0 + s;
-        return h(f);
-    });
+    const float* rows[4];
+    for (int lag = 0; lag < 4; ++lag) rows[lag] = ring + static_cast<size_t>((head - lag + 4) & 3) * kpad;
+    gather_pairs(sm, false, nbr, nv, 1.f / sigma, [&](int si) { return si < ns ? s0 + si : -1; },
+                 [&](int, int lag) { return rows[lag]; });
     __syncthreads();
     forward_tile(sm, false);
     const float* Y = reinterpret_cast<const float*>(sm + Smem::Y);
     for (int q = threadIdx.x; q < ns * NO; q += kThreads) {
         const int s = q / NO, o = q - s * NO;
         const int idx = o * nv + s0 + s;
-        s_pred[idx] = __fmaf_rn(sigma, Y[q], hf.rows[0][idx]);
+        s_pred[idx] = __fmaf_rn(sigma, Y[q], rows[0][idx]);
     }
 }
 
