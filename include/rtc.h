@@ -106,7 +106,10 @@ const char* rtc_last_error(const rtc_handle* h);
  * Errors: RTC_EINVAL (bad geometry or parameters), RTC_ENOMEM, RTC_EDEVICE. */
 int rtc_create(const rtc_config* cfg, rtc_handle** out);
 
-/* Release everything the handle owns.  NULL is accepted. */
+/* Release everything the handle owns.  NULL is accepted.  Called while any
+ * rtc_run_loop is running (from its callbacks, or from another thread), the
+ * release is queued and carried out when the last running loop returns: freeing
+ * device memory waits for the device, which would wait for the loop. */
 int rtc_destroy(rtc_handle* h);
 
 /* Replace the subaperture map.  rc: host int32 [n_valid][2] of (row, col) grid
@@ -188,6 +191,22 @@ int rtc_reconstruct_async(rtc_handle* h, const float* d_slopes, float* d_dm_out,
  * done, and report any device error.  Errors: RTC_EDEVICE. */
 int rtc_synchronize(rtc_handle* h, void* stream);
 
+/* Asymmetric subaperture allocation (Sec. 2.3.3, Fig. 6 (d)) for frames that
+ * arrive in n_bands bands of pixel rows, band_interval_us apart (the banded
+ * publication of rtc_run_loop).  The matrix is cut into slices of consecutive
+ * subapertures, one per block of the fused kernels; by default the slices are
+ * equal.  With a readout model the cut gives the subapertures of the last rows
+ * small slices of their own and those that arrive early large ones (at most twice
+ * the mean), so that every block finishes at about the same time after the last
+ * band and last pixel -> DM latency drops.  The resident matrix, if any, is
+ * re-laid out on the device; the model also applies to later rtc_load_cmat calls.
+ * n_bands = 0 or 1 restores equal slices.  Results depend on the cut only through
+ * the order of the partial sums, and are the same for rtc_process_frame and
+ * rtc_run_loop under any cut.  Errors: RTC_EINVAL (n_bands outside 0 .. H,
+ * band_interval_us outside [0, 1e6]), RTC_ENOMEM, RTC_EDEVICE (the matrix is then
+ * unloaded). */
+int rtc_set_readout(rtc_handle* h, int32_t n_bands, double band_interval_us);
+
 /* ---- persistent real-time loop ---------------------------------------------
  * The paper's RTC runs its threads continuously and hands work over through
  * spinning on flags rather than sleeping (Sec. 2.3.2); latency is measured from
@@ -195,14 +214,18 @@ int rtc_synchronize(rtc_handle* h, void* stream);
  * rtc_run_loop is the GPU form: one persistent kernel keeps calibration, matrix
  * and integrator resident and loops over frames.  A host thread publishes each
  * frame in a ring of pinned, device-mapped buffers by setting a sequence flag;
- * the kernel's blocks spin (bounded) on that flag, read the pixels directly from
- * host memory, compute the DM commands, write them to mapped host memory and
- * publish a completion record with device timestamps. */
+ * the kernel's blocks spin (bounded) on that flag, each copies the pixels of its
+ * own subapertures from host memory, computes its share of the DM commands, and
+ * the commands go to mapped host memory with a completion record carrying device
+ * timestamps. */
 
 #define RTC_LOOP_SLOTS 8            /* frame slots in the host ring */
 
 /* Fill dst (pinned host memory, uint16 [n_wfs][H][W]) with frame k.  Return 0,
- * or non-zero to end the loop early.  Called on a library-owned thread. */
+ * or non-zero to end the loop early.  Called on a library-owned thread.  The
+ * source and sink callbacks must not make CUDA calls that wait for the device
+ * (cudaDeviceSynchronize, cudaFree, ...): the device is running the loop, which
+ * waits for them.  The library's own release calls are safe (they are queued). */
 typedef int (*rtc_frame_source)(void* user, uint64_t k, uint16_t* dst);
 
 /* Receives the DM commands (float32 [nact], valid during the call) of frame k,
@@ -221,12 +244,21 @@ typedef struct rtc_loop_config {
     void* sink_user;
     int64_t* e2e_ns;             /* [n_frames] publish -> DM visible on the host, or NULL */
     int64_t* dev_ns;             /* [n_frames] frame seen -> DM written, device clock, or NULL */
+    int32_t n_bands;             /* 0 or 1: each frame is published whole.  2 .. H: in
+                                    n_bands bands of pixel rows, top to bottom, as a
+                                    rolling-shutter camera reads out; band j holds rows
+                                    floor(H j / n_bands) .. floor(H (j+1) / n_bands) - 1 of
+                                    every WFS.  Each block of the kernel starts as soon as
+                                    the rows its subapertures cover have arrived (the
+                                    paper's processing of pixels during readout, Sec. 2.2). */
+    double band_interval_us;     /* host time between the publication of successive bands */
 } rtc_loop_config;
 
 /* Latency statistics of one rtc_run_loop call.  "e2e": host clock, from the flag
- * that publishes the frame to the moment the host sees the completion record
- * (the DM commands are in host memory).  "dev": device clock, from the first
- * block seeing the frame to the last block finishing its DM commands. */
+ * that publishes the frame (with bands: its last band) to the moment the host
+ * sees the completion record (the DM commands are in host memory).  "dev": device
+ * clock, from the moment the last block has the pixel rows it needs to the last
+ * block finishing its DM commands: last pixel seen -> DM demand written. */
 typedef struct rtc_stats {
     uint64_t frames;             /* frames completed */
     double frames_per_s;         /* completed frames / (last completion - first publish) */
@@ -259,7 +291,8 @@ typedef struct rtc_server rtc_server;
 /* Errors: RTC_EINVAL (max_slots < 1 or > 32, budget <= 0, device), RTC_ENOMEM. */
 int rtc_server_create(int32_t device, int32_t max_slots, int64_t mem_budget_bytes, rtc_server** out);
 
-/* Wait for running jobs, then release the server (not the handles). */
+/* Wait for running jobs, then release the server (not the handles).  Queued
+ * like rtc_destroy while an rtc_run_loop is running. */
 int rtc_server_destroy(rtc_server* s);
 
 /* Admit a job: frames host uint16 [n_frames][n_wfs][H][W] (pinned memory keeps the
@@ -307,6 +340,7 @@ typedef struct rtc_mlp rtc_mlp;
 
 /* A network on `device` with all parameters zero.  Errors: RTC_EINVAL, RTC_ENOMEM. */
 int rtc_mlp_create(int32_t device, rtc_mlp** out);
+/* Release the network; queued like rtc_destroy while an rtc_run_loop is running. */
 int rtc_mlp_destroy(rtc_mlp* m);
 
 /* Host float32 [RTC_MLP_NPARAMS] in/out; setting resets the Adam state and step. */

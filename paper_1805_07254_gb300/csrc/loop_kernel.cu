@@ -2,32 +2,42 @@
 // frame after frame, in one cooperative launch.
 //
 // The paper's RTC keeps its worker threads running and synchronises them by
-// spinning on flags instead of sleeping (Sec. 2.3.2).  Here every block keeps
-// running across frames:
-//   1. thread 0 of each block spins (bounded, 2 s) on the frame's sequence flag
-//      in pinned host memory (a system-scope acquire load); a stop value ends
-//      the loop;
-//   2. the consumer warps copy the block's share of the frame from the host ring
-//      into a device staging buffer with the widest loads the layout allows
-//      (16 bytes for ELT frames), bypassing the caches (the slot is rewritten
-//      between its uses); a bounded grid barrier makes the whole frame visible,
-//      and the consumers compute the slopes of the block's subapertures from it
-//      through L2 into shared memory (one coalesced pass over the host link
-//      instead of a few scattered bytes per pixel row);
+// spinning on flags instead of sleeping (Sec. 2.3.2), and starts on the pixels of
+// a frame while the camera is still reading it out (Sec. 2.2).  Here every block
+// keeps running across frames:
+//   1. thread 0 of each block spins (bounded, 2 s) on the frame slot's sequence
+//      word in pinned host memory (a system-scope acquire load) until the band of
+//      pixel rows that completes the block's subapertures has been published; a
+//      stop value ends the loop;
+//   2. the consumer warps copy the block's own pixels -- the sorted list of
+//      copy units (16 bytes for ELT frames) that its subapertures' rows cover,
+//      built on the host at launch -- from the host slot into a device staging
+//      buffer, bypassing the caches (the slot is rewritten between its uses), and
+//      compute the block's slopes from it through L2 into shared memory.  No block
+//      waits for another: a frame's early bands are turned into slopes and into
+//      partial DM vectors while later bands are still arriving;
 //   3. with the learned predictor on (PRED), the measured slopes go to the next
 //      row of the handle's history ring, a grid barrier makes them visible, and
 //      each block replaces its subapertures' slopes by their prediction
 //      (pred_tile.cuh);
-//   4. each block multiplies its matrix slices by its own slopes (no wait for
-//      other blocks), a grid barrier publishes the partial DM vectors, and each
-//      block sums and integrates its share of the rows (stream_mvm.cuh); DM
-//      commands go to the device state and to the frame's slot in mapped host
-//      memory;
-//   5. the last block to finish publishes the completion record (sequence,
-//      device time the frame was seen, device time the commands were written).
+//   4. each block multiplies its matrix slices by its own slopes, a grid barrier
+//      publishes the partial DM vectors, and each block sums and integrates its
+//      share of the rows (stream_mvm.cuh); DM commands go to the device state and
+//      to the frame's slot in mapped host memory;
+//   5. the last block to finish publishes the completion record (sequence, the
+//      latest device time at which a block had its rows, device time the commands
+//      were written).
 // The producer warp streams the matrix frame after frame; its barrier phases
 // continue across frames, so the next frame's first tiles are already in flight
 // while the kernel waits for the frame.
+//
+// Two blocks may both copy a unit that straddles their subapertures; they write
+// the same bytes of the same frame.  A block only starts copying frame k + 1 after
+// the grid barrier of frame k, which every block reaches after its pixel stage, so
+// no copy overwrites pixels another block is still reading.
+
+#include <algorithm>
+#include <vector>
 
 #include "pixel.cuh"
 #include "pred_tile.cuh"
@@ -46,20 +56,60 @@ struct LoopArgs {
     const uint16_t* frames;            // mapped host ring [nslot][frame_elems]
     unsigned long long frame_elems;
     uint16_t* stage;                   // device [frame_elems]: this frame's pixels
-    int copy_unit;                     // bytes per copy load: 16, 4 or 2
-    const unsigned long long* seq;     // mapped host [nslot]: frame k published as k + 1
+    int copy_unit;                     // bytes per copy unit: 16, 4 or 2
+    const unsigned* units;             // copy units (frame offset / copy_unit) of all blocks
+    const int4* blk;                   // [G] first unit, end unit, band that completes the block
+    int n_bands;                       // bands per frame: frame k band j is k * n_bands + j + 1
+    const unsigned long long* seq;     // mapped host [nslot]: bands published
     float* dm_ring;                    // mapped host [nslot][nact]
     rtc_loop_done* done;               // mapped host [nslot]
     float* s_buf;                      // device [2][kpad]
     unsigned long long* gridbar;       // device, zero at launch
     unsigned long long* donectr;       // device, zero at launch
-    unsigned long long* t_seen;        // device [2]
+    unsigned long long* t_seen;        // device [2], zero at launch
     unsigned long long n_frames;
     int nslot;
     int kpad;
     rtc_pred::PredArgs pa;             // PRED only
     int head0;                         // PRED: ring row of the newest vector at launch
 };
+
+// Units a consumer thread keeps in registers across frames; a block with more
+// than kUnitRegs * kConsumers units reads the rest from the table every frame.
+constexpr int kUnitRegs = 2;
+constexpr unsigned kNoUnit = ~0u;
+
+// The block's copy units of one frame: host slot -> staging, all loads issued
+// before the stores.
+template <typename V>
+__device__ __forceinline__ void copy_units(const uint16_t* frame, uint16_t* stage, const unsigned* units,
+                                           int f1, const unsigned (&ur)[kUnitRegs], int fo) {
+    const V* src = reinterpret_cast<const V*>(frame);
+    V* dst = reinterpret_cast<V*>(stage);
+    V v[kUnitRegs];
+#pragma unroll
+    for (int j = 0; j < kUnitRegs; ++j)
+        if (ur[j] != kNoUnit) v[j] = __ldcv(src + ur[j]);
+    // units beyond the registers, two per thread in flight
+    for (int f = fo; f < f1; f += 2 * kConsumers) {
+        unsigned u[2];
+        V w[2];
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            const int fj = f + j * kConsumers;
+            u[j] = fj < f1 ? __ldg(units + fj) : kNoUnit;
+        }
+#pragma unroll
+        for (int j = 0; j < 2; ++j)
+            if (u[j] != kNoUnit) w[j] = __ldcv(src + u[j]);
+#pragma unroll
+        for (int j = 0; j < 2; ++j)
+            if (u[j] != kNoUnit) __stcg(dst + u[j], w[j]);
+    }
+#pragma unroll
+    for (int j = 0; j < kUnitRegs; ++j)
+        if (ur[j] != kNoUnit) __stcg(dst + ur[j], v[j]);
+}
 
 __device__ __forceinline__ unsigned long long ld_acquire_sys(const unsigned long long* p) {
     unsigned long long v;
@@ -98,59 +148,71 @@ __global__ void __launch_bounds__(kThreads, 1) loop_kernel(LoopArgs L) {
     }
 
     clear_local(L.mv, pl, tid);         // the padding of the local slopes stays zero
+    // integrator state and row scales of the block's rows: the reduction keeps the
+    // shared copy of the state current from frame to frame
+    prefetch_rows<DT>(L.mv, pl, tid);
+    // the block's calibration data (subaperture-major, contiguous), 128-byte lines
+    const int npp = L.px.npx * L.px.npx;
+    const long long cal_lines = (static_cast<long long>(pl.g1 - pl.g0) * npp * 4 + 127) / 128;
     const int slot_lane = 2 * (tid >> 5) + ((tid >> 4) & 1);
-    constexpr unsigned long long kBarriers = PRED ? 3 : 2;     // grid barriers per frame
-    // the block's share of the frame's copy units
-    const long long n_units = static_cast<long long>(L.frame_elems * 2 / L.copy_unit);
-    const long long u0 = n_units * blockIdx.x / gridDim.x;
-    const long long u1 = n_units * (blockIdx.x + 1) / gridDim.x;
+    constexpr unsigned long long kBarriers = PRED ? 2 : 1;     // grid barriers per frame
     int tile = 0;
     for (unsigned long long k = 0; k < L.n_frames; ++k) {
         const int slot = static_cast<int>(k % L.nslot);
-        // 1. wait for frame k
+        // the block's first copy units, fetched while thread 0 waits for the frame
+        // (reloaded every frame, so that they hold no registers across the rest)
+        const int4 bk = __ldg(L.blk + blockIdx.x);
+        // warm L2 with the block's dark and gain values while the frame is awaited
+        for (long long c = tid; c < 2 * cal_lines; c += kConsumers) {
+            const float* base = c < cal_lines ? L.px.dark : L.px.gainmap;
+            const long long line = c < cal_lines ? c : c - cal_lines;
+            asm volatile("prefetch.global.L2::evict_last [%0];" ::"l"(
+                reinterpret_cast<const char*>(base + static_cast<size_t>(pl.g0) * npp) + line * 128));
+        }
+        unsigned ur[kUnitRegs];
+#pragma unroll
+        for (int j = 0; j < kUnitRegs; ++j) {
+            const int f = bk.x + tid + j * kConsumers;
+            ur[j] = f < bk.y ? __ldg(L.units + f) : kNoUnit;
+        }
+        // 1. wait for the band of frame k that completes the block's subapertures
         if (tid == 0) {
             int stop = 0;
+            const unsigned long long want = k * static_cast<unsigned long long>(L.n_bands) + bk.z + 1;
             const unsigned long long t0 = global_ns();
+            unsigned long long t = t0;
             while (true) {
                 const unsigned long long v = ld_acquire_sys(L.seq + slot);
+                t = global_ns();
                 if (v == kStop) {
                     stop = 1;
                     break;
                 }
-                if (v >= k + 1) break;
-                if (global_ns() - t0 > kFrameWaitNs) {
+                if (v >= want) break;
+                if (t - t0 > kFrameWaitNs) {
                     atomicExch(L.mv.status, RTC_ETIMEDOUT);
                     stop = 1;
                     break;
                 }
             }
-            if (blockIdx.x == 0 && !stop) L.t_seen[k & 1] = global_ns();
+            if (!stop) atomicMax(L.t_seen + (k & 1), t);
             if (stop) sh.abort_flag = 1;            // the producer stops too
             stop_now = stop;
         }
         consumer_sync();
         if (stop_now) break;
 
-        // 2. the block's share of the frame into device memory, then the block's
-        //    slopes from it, into the local vector (and the global one)
+        // 2. the block's pixels into device memory, then the block's slopes from
+        //    them, into the local vector (and the global one)
         const uint16_t* frame = L.frames + static_cast<size_t>(slot) * L.frame_elems;
-        if (L.copy_unit == 16) {
-            const uint4* src = reinterpret_cast<const uint4*>(frame);
-            uint4* dst = reinterpret_cast<uint4*>(L.stage);
-            for (long long c = u0 + tid; c < u1; c += kConsumers) __stcg(dst + c, __ldcv(src + c));
-        } else if (L.copy_unit == 4) {
-            const unsigned* src = reinterpret_cast<const unsigned*>(frame);
-            unsigned* dst = reinterpret_cast<unsigned*>(L.stage);
-            for (long long c = u0 + tid; c < u1; c += kConsumers) __stcg(dst + c, __ldcv(src + c));
-        } else {
-            for (long long c = u0 + tid; c < u1; c += kConsumers)
-                __stcg(reinterpret_cast<unsigned short*>(L.stage) + c,
-                       __ldcv(reinterpret_cast<const unsigned short*>(frame) + c));
-        }
+        const int f_over = bk.x + tid + kUnitRegs * kConsumers;
+        if (L.copy_unit == 16)
+            copy_units<uint4>(frame, L.stage, L.units, bk.y, ur, f_over);
+        else if (L.copy_unit == 4)
+            copy_units<unsigned>(frame, L.stage, L.units, bk.y, ur, f_over);
+        else
+            copy_units<unsigned short>(frame, L.stage, L.units, bk.y, ur, f_over);
         consumer_sync();
-        if (tid == 0) grid_barrier(L.gridbar, G * (kBarriers * k + 1), L.mv.status, &sh.abort_flag);
-        consumer_sync();
-        if (sh.abort_flag) break;
         const int head = (L.head0 + 1 + static_cast<int>(k & 3)) & 3;
         float* s_k = PRED ? L.pa.ring + static_cast<size_t>(head) * L.kpad
                           : L.s_buf + static_cast<size_t>(k & 1) * L.kpad;
@@ -166,13 +228,12 @@ __global__ void __launch_bounds__(kThreads, 1) loop_kernel(LoopArgs L) {
                 pl.loc[iy] = sxy.y;
             }
         }
-        prefetch_rows<DT>(L.mv, pl, tid);
 
         // 3. with the predictor: every block's measured slopes in the history ring,
         //    then the prediction of the block's own subapertures
         if (PRED) {
             consumer_sync();
-            if (tid == 0) grid_barrier(L.gridbar, G * (kBarriers * k + 2), L.mv.status, &sh.abort_flag);
+            if (tid == 0) grid_barrier(L.gridbar, G * (kBarriers * k + 1), L.mv.status, &sh.abort_flag);
             consumer_sync();
             if (sh.abort_flag) break;
             rtc_pred::predict(L.pa, pl.scratch, tid, pl.g0, pl.g1, head);
@@ -196,7 +257,9 @@ __global__ void __launch_bounds__(kThreads, 1) loop_kernel(LoopArgs L) {
             const unsigned long long prev = atomicAdd(L.donectr, 1ull);
             if (prev + 1 == G * (k + 1)) {
                 rtc_loop_done* d = L.done + slot;
-                d->t_seen = __ldcg(L.t_seen + (k & 1));
+                // the latest time a block had its rows; cleared for frame k + 2, whose
+                // blocks start after the grid barrier of frame k + 1
+                d->t_seen = atomicExch(L.t_seen + (k & 1), 0ull);
                 d->t_done = global_ns();
                 __threadfence_system();
                 st_release_sys(&d->seq, k + 1);
@@ -212,11 +275,65 @@ cudaError_t launch_t(const Launch& Lc, LoopArgs a, cudaStream_t st) {
                                        dim3(Lc.G), dim3(kThreads), args, Lc.smem, st);
 }
 
+// The copy units and the completing band of every block of a G-block launch: for
+// each run of the block's subapertures that are neighbours in one row of the
+// subaperture grid, the units that the run's pixel rows cover; sorted and without
+// repeats, so that neighbouring threads read neighbouring units.
+int build_ingest(rtc_handle* h, int G, int unit, int n_bands) {
+    const int S = h->sl_S, nv = h->n_valid, npx = h->cfg.npx, side = h->side;
+    std::vector<unsigned> units;
+    std::vector<int4> blk(G);
+    std::vector<unsigned> mine;
+    for (int b = 0; b < G; ++b) {
+        const int g0 = h->sl_g0[static_cast<long long>(S) * b / G];
+        const int g1 = h->sl_g0[static_cast<long long>(S) * (b + 1) / G];
+        mine.clear();
+        int last_row = 0;
+        for (int gi = g0; gi < g1;) {
+            const int w = gi / nv, i = gi - w * nv;
+            const int r = h->rc[2 * i], c = h->rc[2 * i + 1];
+            int n = 1;
+            while (gi + n < g1 && (gi + n) / nv == w && h->rc[2 * (i + n)] == r &&
+                   h->rc[2 * (i + n) + 1] == c + n)
+                ++n;
+            for (int y = 0; y < npx; ++y) {
+                const long long row = static_cast<long long>(w) * side + static_cast<long long>(r) * npx + y;
+                const long long b0 = (row * side + static_cast<long long>(c) * npx) * 2;
+                const long long b1 = b0 + static_cast<long long>(n) * npx * 2;
+                for (long long u = b0 / unit; u <= (b1 - 1) / unit; ++u) mine.push_back(static_cast<unsigned>(u));
+            }
+            last_row = std::max(last_row, r * npx + npx - 1);
+            gi += n;
+        }
+        std::sort(mine.begin(), mine.end());
+        mine.erase(std::unique(mine.begin(), mine.end()), mine.end());
+        // row y belongs to band j when floor(side j / n) <= y < floor(side (j+1) / n)
+        const int band = static_cast<int>(((static_cast<long long>(last_row) + 1) * n_bands - 1) / side);
+        blk[b] = make_int4(static_cast<int>(units.size()), static_cast<int>(units.size() + mine.size()), band, 0);
+        units.insert(units.end(), mine.begin(), mine.end());
+    }
+    if (units.empty()) units.push_back(0);
+    if (units.size() > h->units_cap) {
+        if (h->d_units) cudaFree(h->d_units);
+        h->d_units = nullptr;
+        h->units_cap = 0;
+        if (cudaMalloc(&h->d_units, units.size() * sizeof(unsigned)) != cudaSuccess) return RTC_ENOMEM;
+        h->units_cap = units.size();
+    }
+    if (!h->d_blk && cudaMalloc(&h->d_blk, static_cast<size_t>(h->dev_sms) * sizeof(int4)) != cudaSuccess)
+        return RTC_ENOMEM;
+    if (cudaMemcpy(h->d_units, units.data(), units.size() * sizeof(unsigned), cudaMemcpyHostToDevice) !=
+            cudaSuccess ||
+        cudaMemcpy(h->d_blk, blk.data(), G * sizeof(int4), cudaMemcpyHostToDevice) != cudaSuccess)
+        return RTC_EDEVICE;
+    return RTC_OK;
+}
+
 template <int DT>
 cudaError_t launch_dt(rtc_handle* h, const LoopLaunch& ll, cudaStream_t st) {
     const bool pred = h->pred_on;
     const Launch Lc = plan_launch(h, pred ? rtc_pred::kSmemBytes : 0);
-    if (!Lc.ok) return cudaErrorInvalidValue;
+    if (!Lc.ok || Lc.G > h->dev_sms) return cudaErrorInvalidValue;
     LoopArgs a{};
     a.px = pixel_args(h, nullptr, nullptr);
     a.mv = make_args(h, nullptr, nullptr, Lc);
@@ -226,6 +343,12 @@ cudaError_t launch_dt(rtc_handle* h, const LoopLaunch& ll, cudaStream_t st) {
     const size_t fbytes = ll.frame_elems * 2;
     const uintptr_t bases = reinterpret_cast<uintptr_t>(ll.d_frames) | reinterpret_cast<uintptr_t>(h->d_frame);
     a.copy_unit = (fbytes % 16 == 0 && bases % 16 == 0) ? 16 : (fbytes % 4 == 0 && bases % 4 == 0) ? 4 : 2;
+    const int rc = build_ingest(h, Lc.G, a.copy_unit, ll.n_bands);
+    if (rc == RTC_ENOMEM) return cudaErrorMemoryAllocation;
+    if (rc != RTC_OK) return cudaErrorUnknown;
+    a.units = h->d_units;
+    a.blk = h->d_blk;
+    a.n_bands = ll.n_bands;
     a.seq = ll.d_seq;
     a.dm_ring = ll.d_dm;
     a.done = ll.d_done;

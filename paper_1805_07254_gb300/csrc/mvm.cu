@@ -236,6 +236,22 @@ __global__ void layout_raw_kernel(const unsigned char* __restrict__ src, int nco
     }
 }
 
+__global__ void relayout_kernel(const unsigned char* __restrict__ src, const int2* __restrict__ src_map,
+                                const long long* __restrict__ src_off, const int* __restrict__ src_rb,
+                                int ncol, int esize, const int2* __restrict__ dst_map,
+                                const long long* __restrict__ dst_off, const int* __restrict__ dst_rb,
+                                unsigned char* __restrict__ dst) {
+    const int row = blockIdx.x;
+    for (int c = threadIdx.x; c < ncol; c += blockDim.x) {
+        const int2 a = src_map[c], b = dst_map[c];
+        const unsigned char* q = src + src_off[a.x] + static_cast<size_t>(row) * src_rb[a.x] +
+                                 static_cast<size_t>(a.y) * esize;
+        unsigned char* p = dst + dst_off[b.x] + static_cast<size_t>(row) * dst_rb[b.x] +
+                           static_cast<size_t>(b.y) * esize;
+        for (int k = 0; k < esize; ++k) p[k] = q[k];
+    }
+}
+
 template <int DT>
 void launch_raw_t(dim3 grid, const uint4* M, int kpad, int nact, const float* d_s, const float* d_scale,
                   int ksplit, float* d_partial, unsigned* d_count, float* d_a, float* d_dm_out,
@@ -304,5 +320,15 @@ cudaError_t launch_layout(int src, int store, const void* d_src, int nact, int n
         default:
             return cudaErrorInvalidValue;
     }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_relayout(int esize, const void* d_old, const int2* d_old_colmap, const long long* d_old_off,
+                            const int* d_old_rowbytes, int nact, int ncol, const int2* d_new_colmap,
+                            const long long* d_new_off, const int* d_new_rowbytes, void* d_new, cudaStream_t st) {
+    if (nact <= 0 || ncol <= 0) return cudaSuccess;
+    relayout_kernel<<<nact, 256, 0, st>>>(static_cast<const unsigned char*>(d_old), d_old_colmap, d_old_off,
+                                          d_old_rowbytes, ncol, esize, d_new_colmap, d_new_off, d_new_rowbytes,
+                                          static_cast<unsigned char*>(d_new));
     return cudaGetLastError();
 }

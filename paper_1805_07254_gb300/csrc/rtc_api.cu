@@ -8,6 +8,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -90,6 +91,132 @@ int dtype_size(int dt) {
         case RTC_INT8: return 1;
         default: return 0;
     }
+}
+
+// Asymmetric subaperture allocation (Sec. 2.3.3, Fig. 6 (d)): the per-block cost
+// model.  A block that owns n subapertures needs, after the last of their pixel
+// rows has arrived, about n * (2 nact esz / kAllocSmGBs + kAllocPixelNs) ns: its
+// matrix columns streamed by one SM, plus its share of the pixel stage.
+constexpr long long kAllocSmGBs = 60;       // bytes per ns one SM streams
+constexpr long long kAllocPixelNs = 50;
+constexpr int kAllocMaxWidth = 2;           // largest slice, in mean slice widths
+
+// First subaperture of each slice (the last entry is the subaperture count).
+// Without a readout model: equal slices of consecutive subapertures, one per SM.
+// With one (n_bands bands of pixel rows, interval_ns apart): the cut that lets
+// every slice finish by the earliest common time T, found by bisection on T; for
+// a given T the slices are cut from the end of the subaperture order, each as
+// long as the latest arrival among its subapertures plus its cost stays within T
+// (and within kAllocMaxWidth mean widths), so that the subapertures of the last
+// rows get slices of their own and those that arrive early share large ones.
+std::vector<int> slice_bounds(const rtc_handle* h, int esz) {
+    const int nt = h->n_valid * h->cfg.n_wfs;
+    const int S = std::min(h->dev_sms, nt);
+    std::vector<int> g0(S + 1);
+    for (int s = 0; s <= S; ++s) g0[s] = static_cast<int>(static_cast<long long>(nt) * s / S);
+    if (h->ro_bands <= 1 || nt <= S) return g0;
+    const int nv = h->n_valid, npx = h->cfg.npx, side = h->side, nb = h->ro_bands;
+    std::vector<long long> t(nt);
+    long long t_last = 0;
+    for (int gi = 0; gi < nt; ++gi) {
+        const int i = gi % nv;
+        const long long band = ((static_cast<long long>(h->rc[2 * i]) * npx + npx) * nb - 1) / side;
+        t[gi] = band * h->ro_interval_ns;
+        t_last = std::max(t_last, t[gi]);
+    }
+    const long long c = 2ll * h->cfg.nact * esz / kAllocSmGBs + kAllocPixelNs;
+    const int wmax = std::max(1, (kAllocMaxWidth * nt + S - 1) / S);
+    auto cut = [&](long long T, std::vector<int>* starts) {
+        int p = nt, k = 0;
+        while (p > 0) {
+            int n = 0;
+            long long tmax = 0;
+            while (p - n > 0 && n < wmax) {
+                const long long tm = std::max(tmax, t[p - n - 1]);
+                if (n > 0 && tm + c * (n + 1) > T) break;
+                tmax = tm;
+                ++n;
+            }
+            p -= n;
+            ++k;
+            if (starts) starts->push_back(p);
+        }
+        return k;
+    };
+    long long lo = t_last + c, hi = t_last + c * nt;   // cut(hi) <= ceil(nt / wmax) <= S
+    if (cut(lo, nullptr) > S) {
+        while (hi - lo > 1) {
+            const long long mid = lo + (hi - lo) / 2;
+            if (cut(mid, nullptr) <= S) hi = mid;
+            else lo = mid;
+        }
+        lo = hi;
+    }
+    std::vector<int> starts;
+    cut(lo, &starts);
+    std::reverse(starts.begin(), starts.end());
+    starts.push_back(nt);
+    return starts;
+}
+
+// The slice table for slice bounds g0, in the handle's host vectors: each slice one
+// contiguous [nact][2 n_s] block (x slopes, then y slopes), rows padded to a
+// multiple of 4 bytes with an access unit (16, 8 or 4 bytes) that divides them an
+// odd number of times.  colmap: column c (WFS w, axis, subaperture i) -> (slice,
+// column within the slice).
+void cut_slices(rtc_handle* h, const std::vector<int>& g0, int esz, std::vector<int2>& colmap) {
+    const int S = static_cast<int>(g0.size()) - 1;
+    const int nact = h->cfg.nact;
+    h->sl_S = S;
+    h->sl_g0 = g0;
+    h->sl_off.resize(S);
+    h->sl_rowbytes.resize(S);
+    h->sl_loc.resize(S + 1);
+    long long off = 0;
+    int loc = 0;
+    for (int s = 0; s < S; ++s) {
+        const int n = g0[s + 1] - g0[s];
+        int rb = (2 * n * esz + 3) / 4 * 4;
+        while (rtc_mvm::row_unit(rb) == 0) rb += 4;       // a bank-conflict-free access unit
+        h->sl_off[s] = off;
+        h->sl_rowbytes[s] = rb;
+        off += (static_cast<long long>(nact) * rb + 15) / 16 * 16;
+        h->sl_loc[s] = loc;
+        loc += (rb / esz + 3) / 4 * 4;
+    }
+    h->sl_loc[S] = loc;
+    h->m_bytes = off;
+    const int nv = h->n_valid, nt = nv * h->cfg.n_wfs;
+    std::vector<int> slice_of(nt);
+    for (int s = 0; s < S; ++s)
+        for (int gi = g0[s]; gi < g0[s + 1]; ++gi) slice_of[gi] = s;
+    colmap.resize(h->nslopes);
+    for (int c = 0; c < h->nslopes; ++c) {
+        const int w = c / (2 * nv), rem = c - w * 2 * nv;
+        const int axis = rem >= nv ? 1 : 0;
+        const int gi = w * nv + (rem - axis * nv);
+        const int sl = slice_of[gi];
+        const int n = g0[sl + 1] - g0[sl];
+        colmap[c] = make_int2(sl, axis * n + (gi - g0[sl]));
+    }
+}
+
+// The slice table to the device.
+cudaError_t upload_slices(rtc_handle* h) {
+    const int S = h->sl_S;
+    cudaError_t e = cudaMalloc(&h->d_sl_off, S * sizeof(long long));
+    if (e == cudaSuccess) e = cudaMalloc(&h->d_sl_rowbytes, S * sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&h->d_sl_g0, (S + 1) * sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&h->d_sl_loc, (S + 1) * sizeof(int));
+    if (e == cudaSuccess)
+        e = cudaMemcpy(h->d_sl_off, h->sl_off.data(), S * sizeof(long long), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(h->d_sl_rowbytes, h->sl_rowbytes.data(), S * sizeof(int), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(h->d_sl_g0, h->sl_g0.data(), (S + 1) * sizeof(int), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(h->d_sl_loc, h->sl_loc.data(), (S + 1) * sizeof(int), cudaMemcpyHostToDevice);
+    return e;
 }
 
 // Default map: subaperture centres inside the annulus obs*n/2 <= r <= n/2,
@@ -206,6 +333,34 @@ int enqueue_step(rtc_handle* h, const uint16_t* d_frame, float* d_dm_out, float*
 
 void rtc_set_global_error(const char* msg) { g_create_error = msg; }
 
+namespace {
+std::mutex g_loop_mu;
+int g_loops = 0;
+std::vector<std::function<void()>> g_deferred;
+}  // namespace
+
+void loop_begin() {
+    std::lock_guard<std::mutex> lock(g_loop_mu);
+    ++g_loops;
+}
+
+void loop_end() {
+    std::vector<std::function<void()>> run;
+    {
+        std::lock_guard<std::mutex> lock(g_loop_mu);
+        if (--g_loops > 0) return;
+        run.swap(g_deferred);
+    }
+    for (auto& f : run) f();
+}
+
+bool release_or_defer(std::function<void()> f) {
+    std::lock_guard<std::mutex> lock(g_loop_mu);
+    if (g_loops == 0) return false;
+    g_deferred.push_back(std::move(f));
+    return true;
+}
+
 extern "C" {
 
 const char* rtc_version(void) { return "librtc 0.1 (sm_103a)"; }
@@ -276,6 +431,7 @@ int rtc_create(const rtc_config* cfg, rtc_handle** out) {
 
 int rtc_destroy(rtc_handle* h) {
     if (!h) return RTC_OK;
+    if (release_or_defer([h] { rtc_destroy(h); })) return RTC_OK;
     DeviceScope ds(h->cfg.device);
     if (h->stream) cudaStreamSynchronize(h->stream);
     free_predictor(h);
@@ -294,6 +450,8 @@ int rtc_destroy(rtc_handle* h) {
     free_dev(h->d_sbuf);
     free_dev(h->d_donectr);
     free_dev(h->d_tseen);
+    free_dev(h->d_units);
+    free_dev(h->d_blk);
     if (h->h_ring) cudaFreeHost(h->h_ring);
     if (h->h_seq) cudaFreeHost(h->h_seq);
     if (h->h_dm_ring) cudaFreeHost(h->h_dm_ring);
@@ -381,55 +539,13 @@ int rtc_load_cmat(rtc_handle* h, const void* M, int32_t nact, int32_t nslopes, i
         h->store = store;
         return RTC_OK;
     }
-    // slice table: S slices of consecutive subapertures, each stored as one
-    // contiguous [nact][2 n_s] block (x slopes, then y slopes), rows padded to a
-    // multiple of 4 bytes with an access unit (16, 8 or 4 bytes) that divides them an
-    // odd number of times
     const int esz = dtype_size(store);
-    const int nt = h->n_valid * h->cfg.n_wfs;
-    const int S = std::min(h->dev_sms, nt);
-    h->sl_S = S;
-    h->sl_g0.resize(S + 1);
-    h->sl_off.resize(S);
-    h->sl_rowbytes.resize(S);
-    h->sl_loc.resize(S + 1);
-    for (int s = 0; s <= S; ++s) h->sl_g0[s] = static_cast<int>(static_cast<long long>(nt) * s / S);
-    long long off = 0;
-    int loc = 0;
-    for (int s = 0; s < S; ++s) {
-        const int n = h->sl_g0[s + 1] - h->sl_g0[s];
-        int rb = (2 * n * esz + 3) / 4 * 4;
-        while (rtc_mvm::row_unit(rb) == 0) rb += 4;       // a bank-conflict-free access unit
-        h->sl_off[s] = off;
-        h->sl_rowbytes[s] = rb;
-        off += (static_cast<long long>(nact) * rb + 15) / 16 * 16;
-        h->sl_loc[s] = loc;
-        loc += (rb / esz + 3) / 4 * 4;
+    std::vector<int2> colmap;
+    cut_slices(h, slice_bounds(h, esz), esz, colmap);
+    if (upload_slices(h) != cudaSuccess) {
+        free_slices(h);
+        return fail(h, RTC_ENOMEM, "cannot allocate the slice table");
     }
-    h->sl_loc[S] = loc;
-    h->m_bytes = off;
-    // column c (WFS w, axis, subaperture i) -> (slice, column within the slice)
-    const int nv = h->n_valid;
-    std::vector<int> slice_of(nt);
-    for (int s = 0; s < S; ++s)
-        for (int gi = h->sl_g0[s]; gi < h->sl_g0[s + 1]; ++gi) slice_of[gi] = s;
-    std::vector<int2> colmap(nslopes);
-    for (int c = 0; c < nslopes; ++c) {
-        const int w = c / (2 * nv), rem = c - w * 2 * nv;
-        const int axis = rem >= nv ? 1 : 0;
-        const int gi = w * nv + (rem - axis * nv);
-        const int sl = slice_of[gi];
-        const int n = h->sl_g0[sl + 1] - h->sl_g0[sl];
-        colmap[c] = make_int2(sl, axis * n + (gi - h->sl_g0[sl]));
-    }
-    RTC_CUDA(h, cudaMalloc(&h->d_sl_off, S * sizeof(long long)));
-    RTC_CUDA(h, cudaMalloc(&h->d_sl_rowbytes, S * sizeof(int)));
-    RTC_CUDA(h, cudaMalloc(&h->d_sl_g0, (S + 1) * sizeof(int)));
-    RTC_CUDA(h, cudaMalloc(&h->d_sl_loc, (S + 1) * sizeof(int)));
-    RTC_CUDA(h, cudaMemcpy(h->d_sl_off, h->sl_off.data(), S * sizeof(long long), cudaMemcpyHostToDevice));
-    RTC_CUDA(h, cudaMemcpy(h->d_sl_rowbytes, h->sl_rowbytes.data(), S * sizeof(int), cudaMemcpyHostToDevice));
-    RTC_CUDA(h, cudaMemcpy(h->d_sl_g0, h->sl_g0.data(), (S + 1) * sizeof(int), cudaMemcpyHostToDevice));
-    RTC_CUDA(h, cudaMemcpy(h->d_sl_loc, h->sl_loc.data(), (S + 1) * sizeof(int), cudaMemcpyHostToDevice));
     if (cudaMalloc(&h->d_M, static_cast<size_t>(h->m_bytes)) != cudaSuccess) {
         h->d_M = nullptr;
         free_slices(h);
@@ -457,6 +573,61 @@ int rtc_load_cmat(rtc_handle* h, const void* M, int32_t nact, int32_t nslopes, i
     cudaFree(d_colmap);
     if (e != cudaSuccess) return fail(h, RTC_EDEVICE, "matrix conversion failed: %s", cudaGetErrorString(e));
     h->store = store;
+    return RTC_OK;
+}
+
+int rtc_set_readout(rtc_handle* h, int32_t n_bands, double band_interval_us) {
+    if (!h) return RTC_EINVAL;
+    if (n_bands < 0 || n_bands > h->side || !(band_interval_us >= 0.0) || !(band_interval_us <= 1e6))
+        return fail(h, RTC_EINVAL, "n_bands must be 0 .. frame height and band_interval_us in [0, 1e6]");
+    DeviceScope ds(h->cfg.device);
+    RTC_CUDA(h, cudaStreamSynchronize(h->stream));
+    h->ro_bands = n_bands;
+    h->ro_interval_ns = static_cast<long long>(band_interval_us * 1e3 + 0.5);
+    if (h->store < 0 || h->sl_S == 0) return RTC_OK;       // the next rtc_load_cmat cuts
+    // the resident matrix from its present slices into the new ones, on the device
+    const int esz = dtype_size(h->store);
+    const int nact = h->cfg.nact, ncol = h->nslopes;
+    std::vector<int2> old_map, new_map;
+    cut_slices(h, h->sl_g0, esz, old_map);                  // the present cut's column map
+    const std::vector<int> g0 = slice_bounds(h, esz);
+    void* old_M = h->d_M;
+    long long* old_off = h->d_sl_off;
+    int* old_rb = h->d_sl_rowbytes;
+    int* old_g0 = h->d_sl_g0;
+    int* old_loc = h->d_sl_loc;
+    h->d_M = nullptr;
+    h->d_sl_off = nullptr;
+    h->d_sl_rowbytes = nullptr;
+    h->d_sl_g0 = nullptr;
+    h->d_sl_loc = nullptr;
+    cut_slices(h, g0, esz, new_map);
+    int2* d_maps = nullptr;
+    cudaError_t e = upload_slices(h);
+    if (e == cudaSuccess) e = cudaMalloc(&h->d_M, static_cast<size_t>(h->m_bytes));
+    if (e == cudaSuccess) e = cudaMemset(h->d_M, 0, static_cast<size_t>(h->m_bytes));
+    if (e == cudaSuccess) e = cudaMalloc(&d_maps, 2 * static_cast<size_t>(ncol) * sizeof(int2));
+    if (e == cudaSuccess)
+        e = cudaMemcpy(d_maps, old_map.data(), ncol * sizeof(int2), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(d_maps + ncol, new_map.data(), ncol * sizeof(int2), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = launch_relayout(esz, old_M, d_maps, old_off, old_rb, nact, ncol, d_maps + ncol, h->d_sl_off,
+                            h->d_sl_rowbytes, h->d_M, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (d_maps) cudaFree(d_maps);
+    cudaFree(old_M);
+    cudaFree(old_off);
+    cudaFree(old_rb);
+    cudaFree(old_g0);
+    cudaFree(old_loc);
+    if (e != cudaSuccess) {
+        free_dev(h->d_M);
+        free_slices(h);
+        h->store = -1;
+        return fail(h, e == cudaErrorMemoryAllocation ? RTC_ENOMEM : RTC_EDEVICE,
+                    "matrix re-cut failed (the matrix must be loaded again): %s", cudaGetErrorString(e));
+    }
     return RTC_OK;
 }
 

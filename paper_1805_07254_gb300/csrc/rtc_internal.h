@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <functional>
 #include <string>
 #include <vector>
 
@@ -34,6 +35,7 @@ struct LoopLaunch {
     rtc_loop_done* d_done;
     unsigned long long n_frames;
     int nslot;
+    int n_bands;                 // >= 1 bands of pixel rows per frame
 };
 
 struct rtc_handle {
@@ -43,6 +45,8 @@ struct rtc_handle {
     int nslopes = 0;            // 2 * n_valid * n_wfs
     int kpad = 0;               // padded matrix row length (elements)
     int store = -1;             // rtc_dtype of the resident matrix, -1 when none
+    int ro_bands = 0;           // readout model of the slice cut (rtc_set_readout): bands,
+    long long ro_interval_ns = 0;   // and time between bands
     float gain = 0.f, leak = 1.f;
     int thr_mode = 0;
     float thr = 0.f;
@@ -82,7 +86,10 @@ struct rtc_handle {
     // persistent loop (allocated by the first rtc_run_loop)
     float* d_sbuf = nullptr;                  // [2][kpad] slope vectors by frame parity
     unsigned long long* d_donectr = nullptr;  // finished-block counter
-    unsigned long long* d_tseen = nullptr;    // [2] device time each frame was seen
+    unsigned long long* d_tseen = nullptr;    // [2] device time the last block had its frame rows
+    unsigned* d_units = nullptr;              // frame copy units of each block (see loop_kernel.cu)
+    size_t units_cap = 0;                     // entries d_units holds
+    int4* d_blk = nullptr;                    // [dev_sms] per block: first unit, end, band, 0
     uint16_t* h_ring = nullptr;               // pinned mapped [RTC_LOOP_SLOTS][n_wfs][H][W]
     unsigned long long* h_seq = nullptr;      // pinned mapped [RTC_LOOP_SLOTS]
     float* h_dm_ring = nullptr;               // pinned mapped [RTC_LOOP_SLOTS][nact]
@@ -144,6 +151,12 @@ cudaError_t launch_layout(int src, int store, const void* d_src, int nact, int n
                           const int2* d_colmap, const long long* d_off, const int* d_rowbytes,
                           float* d_scale, void* d_dst, cudaStream_t st);
 
+// Move a matrix between two slice layouts of the same store (esize bytes per
+// entry): column c from (old_colmap[c]) to (new_colmap[c]).
+cudaError_t launch_relayout(int esize, const void* d_old, const int2* d_old_colmap, const long long* d_old_off,
+                            const int* d_old_rowbytes, int nact, int ncol, const int2* d_new_colmap,
+                            const long long* d_new_off, const int* d_new_rowbytes, void* d_new, cudaStream_t st);
+
 // Read and clear the device status word after `st` drains (RTC_OK or the recorded
 // error, which also restarts the grid-barrier count); set the handle's message.
 int take_status(rtc_handle* h, cudaStream_t st);
@@ -155,6 +168,17 @@ bool rtc_handle_ready(const rtc_handle* h);
 // Device memory the handle holds (matrix, calibration, state, staging).
 int64_t rtc_handle_device_bytes(const rtc_handle* h);
 int fail_handle(rtc_handle* h, int code, const char* msg);
+
+// While a persistent loop runs, a release (rtc_destroy, rtc_mlp_destroy,
+// rtc_server_destroy) would wait for the device and so for the loop, whose kernel
+// in turn waits for frames from the host thread: called from a source or sink
+// callback, or from a garbage collector that runs inside one, it would deadlock
+// until the loop's bounded waits expire.  Releases made while any loop runs are
+// therefore queued and carried out when the last loop has ended.
+void loop_begin();
+void loop_end();
+// Run f now, or queue it if a loop is running; true when queued.
+bool release_or_defer(std::function<void()> f);
 
 // Message returned by rtc_last_error(NULL) for failures of calls without a handle.
 void rtc_set_global_error(const char* msg);

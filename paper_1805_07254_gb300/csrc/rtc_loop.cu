@@ -3,10 +3,14 @@
 // A ring of RTC_LOOP_SLOTS frame slots lives in pinned host memory mapped into the
 // device's address space.  A filler thread writes frame k into slot k % nslot
 // (through the caller's source callback) once the device is done with the frame
-// that used the slot before; the calling thread publishes frame k at its time by
-// a release store of k + 1 into the slot's sequence word, then spins on the
-// slot's completion record and takes the frame's latency.  With a preloaded frame
-// set the slots are filled once and only republished.
+// that used the slot before; the calling thread publishes frame k at its time,
+// band by band (n_bands bands of pixel rows, n_bands = 1 for a whole frame), by
+// release stores of k * n_bands + j + 1 into the slot's sequence word, then spins
+// on the slot's completion record and takes the frame's latency from the last
+// band.  With a preloaded frame set the slots are filled once and only
+// republished.  The pixels are in the slot before the first band is published;
+// the bands only gate when each part of the kernel may read them, as the rows of
+// a rolling readout would.
 
 #include <math.h>
 #include <string.h>
@@ -104,6 +108,11 @@ extern "C" int rtc_run_loop(rtc_handle* h, const rtc_loop_config* cfg, rtc_stats
         return fail_handle(h, RTC_EINVAL, "n_frames must be > 0 and rate_hz finite and >= 0");
     if (!cfg->source && (!cfg->preload || cfg->n_preload < 1 || cfg->n_preload > RTC_LOOP_SLOTS))
         return fail_handle(h, RTC_EINVAL, "give a source callback or 1..RTC_LOOP_SLOTS preloaded frames");
+    if (cfg->n_bands < 0 || cfg->n_bands > h->side || !(cfg->band_interval_us >= 0.0) ||
+        !isfinite(cfg->band_interval_us))
+        return fail_handle(h, RTC_EINVAL, "n_bands must be 0 .. frame height and band_interval_us finite and >= 0");
+    const int nb = std::max(cfg->n_bands, 1);
+    const long long band_ns = static_cast<long long>(cfg->band_interval_us * 1e3);
     memset(stats, 0, sizeof *stats);
 
     int dev_prev = -1;
@@ -116,6 +125,12 @@ extern "C" int rtc_run_loop(rtc_handle* h, const rtc_loop_config* cfg, rtc_stats
             if (d >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != d) cudaSetDevice(d);
         }
     } restore{dev_prev};
+
+    // releases requested while the loop runs wait for its end
+    struct LoopScope {
+        LoopScope() { loop_begin(); }
+        ~LoopScope() { loop_end(); }
+    } loop_scope;
 
     int rc = ensure_buffers(h);
     if (rc != RTC_OK) return rc;
@@ -133,6 +148,7 @@ extern "C" int rtc_run_loop(rtc_handle* h, const rtc_loop_config* cfg, rtc_stats
             memcpy(h->h_ring + i * frame_elems, cfg->preload + i * frame_elems, frame_elems * 2);
     LOOP_CUDA(cudaMemsetAsync(h->d_gridbar, 0, sizeof(unsigned long long), h->stream));
     LOOP_CUDA(cudaMemsetAsync(h->d_donectr, 0, sizeof(unsigned long long), h->stream));
+    LOOP_CUDA(cudaMemsetAsync(h->d_tseen, 0, 2 * sizeof(unsigned long long), h->stream));
     h->grid_epoch = 0;
 
     LoopLaunch ll{};
@@ -143,6 +159,7 @@ extern "C" int rtc_run_loop(rtc_handle* h, const rtc_loop_config* cfg, rtc_stats
     ll.frame_elems = frame_elems;
     ll.n_frames = n;
     ll.nslot = nslot;
+    ll.n_bands = nb;
     LOOP_CUDA(launch_loop(h, ll, h->stream));
 
     // filler: frame k into slot k % nslot once frame k - nslot has left it
@@ -190,9 +207,19 @@ extern "C" int rtc_run_loop(rtc_handle* h, const rtc_loop_config* cfg, rtc_stats
             while (mono_ns() < due) {
             }
         }
+        // bands 0 .. nb - 2 at their times, then the last one, from which the
+        // frame's latency is taken
+        const long long t_band0 = mono_ns();
+        if (k == 0) t_first_pub = t_band0;
+        for (int j = 0; j + 1 < nb; ++j) {
+            while (mono_ns() < t_band0 + j * band_ns) {
+            }
+            store_release(&h->h_seq[slot], k * nb + j + 1);
+        }
+        while (mono_ns() < t_band0 + (nb - 1) * band_ns) {
+        }
         const long long t_pub = mono_ns();
-        if (k == 0) t_first_pub = t_pub;
-        store_release(&h->h_seq[slot], k + 1);
+        store_release(&h->h_seq[slot], (k + 1) * nb);
         // completion record of frame k
         bool ok = true;
         while (load_acquire(&h->h_done[slot].seq) != k + 1) {

@@ -133,6 +133,7 @@ int rtc_mlp_create(int32_t device, rtc_mlp** out) {
 
 int rtc_mlp_destroy(rtc_mlp* m) {
     if (!m) return RTC_OK;
+    if (release_or_defer([m] { rtc_mlp_destroy(m); })) return RTC_OK;
     Dev d(m->device);
     cudaDeviceSynchronize();
     mlp_free(m->w);

@@ -108,6 +108,7 @@ int rtc_server_create(int32_t device, int32_t max_slots, int64_t mem_budget_byte
 
 int rtc_server_destroy(rtc_server* s) {
     if (!s) return RTC_OK;
+    if (release_or_defer([s] { rtc_server_destroy(s); })) return RTC_OK;
     Dev d(s->device);
     for (size_t i = 0; i < s->streams.size(); ++i) {
         if (s->streams[i]) cudaStreamSynchronize(s->streams[i]);

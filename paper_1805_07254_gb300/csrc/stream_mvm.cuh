@@ -51,7 +51,14 @@ namespace rtc_mvm {
 constexpr int kConsumerWarps = 14;
 constexpr int kConsumers = kConsumerWarps * 32;
 constexpr int kThreads = kConsumers + 32;          // + one producer warp
-constexpr int kMaxStages = 8;
+constexpr int kMaxStages = 32;
+// Smallest ring stage the launch plan aims for, in bytes.
+constexpr size_t kMinTileBytes = 32 * 1024;
+// Rows of one slice's tile per consumer thread, at most (narrow slices pack several
+// rows into a stage sized for the widest one).
+constexpr int kMaxRowsPerThread = 32;
+// Largest matrix streamed with the default L2 policy (of the 126 MB L2).
+constexpr long long kL2KeepBytes = 80ll << 20;
 constexpr unsigned long long kWaitNs = 200ull * 1000 * 1000;
 constexpr int kMaxLocalFloats = 8192;              // slopes of a block's slices (32 KB)
 constexpr int kMaxRowFloats = 4096;                // rows a block reduces, at most
@@ -95,12 +102,27 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
+// Bulk copy global -> shared completing on an mbarrier, with an L2 eviction policy.
 __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes,
-                                         uint32_t bar) {
+                                         uint32_t bar, unsigned long long policy) {
     asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-        ::"r"(dst), "l"(src), "r"(bytes), "r"(bar)
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint "
+        "[%0], [%1], %2, [%3], %4;"
+        ::"r"(dst), "l"(src), "r"(bytes), "r"(bar), "l"(policy)
         : "memory");
+}
+// L2 policies for the matrix stream.  A matrix larger than L2 goes through without
+// displacing the calibration maps, frames and partial vectors (evict_first); one
+// that fits beside them keeps the default policy, so that frame after frame it can
+// stay in L2.
+enum L2Policy { kL2Normal = 0, kL2Stream = 1 };
+__device__ __forceinline__ unsigned long long matrix_policy(int mode) {
+    unsigned long long p;
+    if (mode == kL2Stream)
+        asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    else
+        asm volatile("createpolicy.fractional.L2::evict_normal.b64 %0, 1.0;" : "=l"(p));
+    return p;
 }
 __device__ __forceinline__ unsigned long long global_ns() {
     unsigned long long t;
@@ -209,13 +231,14 @@ __device__ __forceinline__ float word_dot(float acc, uint32_t w, const float* s)
 
 // Integrator update of one actuator from its previous state and row scale.
 template <int DT>
-__device__ __forceinline__ void integrate_row(int row, float d, float a_prev, float sc,
-                                              float* __restrict__ a, float* __restrict__ dm_out,
-                                              float gain, float leak) {
+__device__ __forceinline__ float integrate_row(int row, float d, float a_prev, float sc,
+                                               float* __restrict__ a, float* __restrict__ dm_out,
+                                               float gain, float leak) {
     if (RowScaled<DT>::v) d *= sc;
     const float an = fmaf(leak, a_prev, gain * d);
     a[row] = an;
     if (dm_out) dm_out[row] = an;
+    return an;
 }
 
 // ---- plan ----------------------------------------------------------------------
@@ -234,7 +257,8 @@ struct Args {
     Slices sl;
     int nact, n_valid;       // rows; valid subapertures per WFS
     int T, R;                // lanes per row, rows per tile (T * R = kConsumers)
-    int stage_bytes, nst;    // bytes per ring stage, stages
+    int stage_bytes, nst;    // the ring: nst stages of stage_bytes (R rows of the widest slice)
+    int l2_policy;           // L2Policy of the matrix stream
     int region;              // shared scratch bytes of a fused phase (before the slopes)
     int loc_floats;          // floats of the largest block-local slope vector
     int row_floats;          // rows a block reduces, at most
@@ -259,6 +283,7 @@ struct Plan {
     int sb0, sb1;            // slices [sb0, sb1)
     int g0, g1;              // subapertures [g0, g1)
     int r0, r1;              // rows the block reduces
+    int rb0, n0, loc0;       // first slice: bytes per row, subapertures, local offset
     uint32_t ring;           // shared address of the ring
     unsigned char* scratch;  // fused-phase scratch (region bytes)
     float* loc;              // block-local slopes: each slice's x then y block, zero padded
@@ -284,6 +309,10 @@ __device__ __forceinline__ Plan make_plan(const Args& g, unsigned char* smem) {
     pl.sb1 = static_cast<int>(static_cast<long long>(S) * (blockIdx.x + 1) / gridDim.x);
     pl.g0 = g.sl.g0[pl.sb0];
     pl.g1 = g.sl.g0[pl.sb1];
+    // the first slice's layout, read once here rather than on the frame's critical path
+    pl.rb0 = g.sl.rowbytes[pl.sb0];
+    pl.n0 = g.sl.g0[pl.sb0 + 1] - pl.g0;
+    pl.loc0 = g.sl.loc[pl.sb0];
     pl.r0 = static_cast<int>(static_cast<long long>(g.nact) * blockIdx.x / gridDim.x);
     pl.r1 = static_cast<int>(static_cast<long long>(g.nact) * (blockIdx.x + 1) / gridDim.x);
     const int ring_bytes = g.nst * g.stage_bytes;
@@ -299,9 +328,14 @@ __device__ __forceinline__ Plan make_plan(const Args& g, unsigned char* smem) {
 // Where subaperture gi (one of the block's) puts its x and y slopes in the
 // block-local vector.
 __device__ __forceinline__ void local_index(const Args& g, const Plan& pl, int gi, int& ix, int& iy) {
-    int s = pl.sb0;
+    if (gi < pl.g0 + pl.n0) {           // the first slice
+        ix = gi - pl.g0;
+        iy = ix + pl.n0;
+        return;
+    }
+    int s = pl.sb0 + 1;
     while (s + 1 < pl.sb1 && g.sl.g0[s + 1] <= gi) ++s;
-    const int base = g.sl.loc[s] - g.sl.loc[pl.sb0];
+    const int base = g.sl.loc[s] - pl.loc0;
     const int n = g.sl.g0[s + 1] - g.sl.g0[s];
     ix = base + (gi - g.sl.g0[s]);
     iy = ix + n;
@@ -335,6 +369,14 @@ __device__ __forceinline__ void prefetch_rows(const Args& g, const Plan& pl, int
     }
 }
 
+// Rows of slice tiles with rb bytes per row: R rows for the widest slice, a multiple
+// of R that still fits in a stage for narrower ones.  A row is always summed by
+// the same T lanes, so the tile height does not change any result.
+__device__ __forceinline__ int tile_rows(const Args& g, int rb) {
+    const int m = g.stage_bytes / (g.R * rb);
+    return g.R * (m < 1 ? 1 : m > kMaxRowsPerThread ? kMaxRowsPerThread : m);
+}
+
 // One producer thread: stream the block's slices tile by tile into the ring.
 // tl0: the running tile count at entry (barrier phases continue across calls, e.g.
 // frame after frame in a persistent kernel); returns the count at exit.  drain: wait
@@ -345,10 +387,12 @@ __device__ __forceinline__ int produce(const Args& g, const Plan& pl, Shared& sh
                                        bool drain = true, int hold = 0) {
     int tl = tl0;
     bool ok = true;
+    const unsigned long long policy = matrix_policy(g.l2_policy);
     for (int s = pl.sb0; s < pl.sb1 && ok; ++s) {
         const unsigned char* base = g.M + g.sl.off[s];
         const int rb = g.sl.rowbytes[s];
-        for (int row0 = 0; row0 < g.nact; row0 += g.R, ++tl) {
+        const int tr = tile_rows(g, rb);
+        for (int row0 = 0; row0 < g.nact; row0 += tr, ++tl) {
             if (hold > 0 && tl - tl0 == hold && !wait_flag(&sh.release, &sh.abort_flag)) {
                 ok = false;
                 break;
@@ -359,7 +403,7 @@ __device__ __forceinline__ int produce(const Args& g, const Plan& pl, Shared& sh
                 ok = false;
                 break;
             }
-            const int rows = min(g.R, g.nact - row0);
+            const int rows = min(tr, g.nact - row0);
             // the slice is padded to 16 bytes, so the last tile may round up; the tile
             // goes as several copies
             const uint32_t bytes = (static_cast<uint32_t>(rows) * rb + 15u) & ~15u;
@@ -367,7 +411,7 @@ __device__ __forceinline__ int produce(const Args& g, const Plan& pl, Shared& sh
             mbar_expect_tx(fb, bytes);
             const unsigned char* src = base + static_cast<size_t>(row0) * rb;
             for (uint32_t o = 0; o < bytes; o += kCopyBytes)
-                bulk_g2s(pl.ring + st * g.stage_bytes + o, src + o, min(kCopyBytes, bytes - o), fb);
+                bulk_g2s(pl.ring + st * g.stage_bytes + o, src + o, min(kCopyBytes, bytes - o), fb, policy);
         }
     }
     if (!ok && !sh.abort_flag) {
@@ -384,7 +428,7 @@ __device__ __forceinline__ int produce(const Args& g, const Plan& pl, Shared& sh
 // broadcasts: every lane of the warp reads the same unit at the same time).
 template <int EPU>
 __device__ __forceinline__ void load_unit(const float* s, float* r) {
-    if (EPU % 4 == 0) {
+    if constexpr (EPU % 4 == 0) {
 #pragma unroll
         for (int j = 0; j < EPU; j += 4) {
             const float4 v = *reinterpret_cast<const float4*>(s + j);
@@ -393,7 +437,7 @@ __device__ __forceinline__ void load_unit(const float* s, float* r) {
             r[j + 2] = v.z;
             r[j + 3] = v.w;
         }
-    } else if (EPU == 2) {
+    } else if constexpr (EPU == 2) {
         const float2 v = *reinterpret_cast<const float2*>(s);
         r[0] = v.x;
         r[1] = v.y;
@@ -402,46 +446,65 @@ __device__ __forceinline__ void load_unit(const float* s, float* r) {
     }
 }
 
-// Dot product of one slice row (in shared memory at rbase, nunits units of U bytes,
-// lane part of T lanes taking units part, part + T, ...) with the slice's slopes sv.
+// acc += <one U-byte unit of a row at shared address a, its slopes r>, word by word.
 template <int DT, int U>
-__device__ __forceinline__ float row_dot(uint32_t rbase, const float* sv, int nunits, int part, int T) {
+__device__ __forceinline__ float unit_dot(float acc, uint32_t a, const float* r) {
     constexpr int EPW = 4 / Esize<DT>::v;                    // elements per 4-byte word
-    constexpr int EPU = U / Esize<DT>::v;                    // elements per unit
-    float acc = 0.f;
-#pragma unroll 4
-    for (int k = part; k < nunits; k += T) {
-        float r[EPU];
-        load_unit<EPU>(sv + k * EPU, r);
-        if (U == 16) {
-            const uint4 m = lds128(rbase + 16 * k);
-            acc = word_dot<DT>(acc, m.x, r);
-            acc = word_dot<DT>(acc, m.y, r + EPW);
-            acc = word_dot<DT>(acc, m.z, r + 2 * EPW);
-            acc = word_dot<DT>(acc, m.w, r + 3 * EPW);
-        } else if (U == 8) {
-            const uint2 m = lds64(rbase + 8 * k);
-            acc = word_dot<DT>(acc, m.x, r);
-            acc = word_dot<DT>(acc, m.y, r + EPW);
-        } else {
-            acc = word_dot<DT>(acc, lds32(rbase + 4 * k), r);
-        }
+    if constexpr (U == 16) {
+        const uint4 m = lds128(a);
+        acc = word_dot<DT>(acc, m.x, r);
+        acc = word_dot<DT>(acc, m.y, r + EPW);
+        acc = word_dot<DT>(acc, m.z, r + 2 * EPW);
+        acc = word_dot<DT>(acc, m.w, r + 3 * EPW);
+    } else if constexpr (U == 8) {
+        const uint2 m = lds64(a);
+        acc = word_dot<DT>(acc, m.x, r);
+        acc = word_dot<DT>(acc, m.y, r + EPW);
+    } else {
+        acc = word_dot<DT>(acc, lds32(a), r);
     }
     return acc;
 }
 
-// The tiles of one slice; returns the running tile count.
+// Slope floats a consumer lane keeps in registers for one slice.
+constexpr int kSlopeRegs = 16;
+// Units of a row a lane can hold the slopes of: kSlopeRegs / (elements per unit).
+template <int DT, int U>
+struct LaneUnits {
+    static constexpr int v = kSlopeRegs * Esize<DT>::v / U > 0 ? kSlopeRegs * Esize<DT>::v / U : 1;
+};
+
+// The tiles of one slice (rb bytes per row, its slopes at pl.loc + lo); returns the
+// running tile count.  Lane `part` of a row's T lanes takes the row's units part,
+// part + T, ..., in that order, and the T partial sums meet in an xor butterfly.
+// When a lane's units fit (LaneUnits), their slopes stay in registers for the
+// whole slice and the tile is read once; otherwise every unit's slopes come from
+// shared memory.  Both ways add the same terms in the same order.
 template <int DT, int U>
 __device__ __forceinline__ int consume_slice(const Args& g, const Plan& pl, Shared& sh, int tid,
-                                             int tile, int s) {
+                                             int tile, int s, int rb, int lo) {
+    constexpr int EPU = U / Esize<DT>::v;                    // elements per unit
+    constexpr int JM = LaneUnits<DT, U>::v;
     const int lane = tid & 31;
     const int rt = tid / g.T;                                // row of the tile
     const int part = tid - rt * g.T;                         // lane within the row's group
-    const int rb = g.sl.rowbytes[s];
     const int nunits = rb / U;
-    const float* sv = pl.loc + (g.sl.loc[s] - g.sl.loc[pl.sb0]);
+    const float* sv = pl.loc + lo;
     float* out = g.partial + static_cast<size_t>(s) * g.nact;
-    for (int row0 = 0; row0 < g.nact; row0 += g.R, ++tile) {
+    const int tr = tile_rows(g, rb);
+    const bool in_regs = (nunits + g.T - 1) / g.T <= JM;     // the same for the whole block
+    float sr[JM][EPU];
+#pragma unroll
+    for (int j = 0; j < JM; ++j) {
+        const int k = part + j * g.T;
+        if (in_regs && k < nunits) {
+            load_unit<EPU>(sv + k * EPU, sr[j]);
+        } else {
+#pragma unroll
+            for (int e = 0; e < EPU; ++e) sr[j][e] = 0.f;
+        }
+    }
+    for (int row0 = 0; row0 < g.nact; row0 += tr, ++tile) {
         const int st = tile % g.nst;
         const bool ok = __all_sync(0xffffffffu, wait_phase(smem_addr(&sh.full_bar[st]),
                                                             (tile / g.nst) & 1, &sh.abort_flag));
@@ -452,12 +515,59 @@ __device__ __forceinline__ int consume_slice(const Args& g, const Plan& pl, Shar
             }
             continue;     // skip the work but keep reaching the block's barriers
         }
-        const int row = row0 + rt;
-        float acc = 0.f;
-        if (row < g.nact)
-            acc = row_dot<DT, U>(pl.ring + st * g.stage_bytes + rt * rb, sv, nunits, part, g.T);
-        for (int off = g.T >> 1; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
-        if (part == 0 && row < g.nact) out[row] = acc;
+        const uint32_t stage = pl.ring + st * g.stage_bytes;
+        // rows of this tile per lane group: the same count on every lane
+        const int iters = (min(tr, g.nact - row0) + g.R - 1) / g.R;
+        if (in_regs) {
+            int i = 0;
+            for (; i + 2 <= iters; i += 2) {                 // two rows in flight
+                const int ra = rt + i * g.R, rbw = ra + g.R;
+                const bool va = row0 + ra < g.nact, vb = row0 + rbw < g.nact;
+                float acc0 = 0.f, acc1 = 0.f;
+#pragma unroll
+                for (int j = 0; j < JM; ++j) {
+                    const int k = part + j * g.T;
+                    if (k < nunits) {
+                        if (va) acc0 = unit_dot<DT, U>(acc0, stage + ra * rb + k * U, sr[j]);
+                        if (vb) acc1 = unit_dot<DT, U>(acc1, stage + rbw * rb + k * U, sr[j]);
+                    }
+                }
+                for (int off = g.T >> 1; off > 0; off >>= 1) {
+                    acc0 += __shfl_xor_sync(0xffffffffu, acc0, off);
+                    acc1 += __shfl_xor_sync(0xffffffffu, acc1, off);
+                }
+                if (part == 0 && va) out[row0 + ra] = acc0;
+                if (part == 0 && vb) out[row0 + rbw] = acc1;
+            }
+            if (i < iters) {
+                const int ra = rt + i * g.R;
+                const bool va = row0 + ra < g.nact;
+                float acc0 = 0.f;
+#pragma unroll
+                for (int j = 0; j < JM; ++j) {
+                    const int k = part + j * g.T;
+                    if (k < nunits && va) acc0 = unit_dot<DT, U>(acc0, stage + ra * rb + k * U, sr[j]);
+                }
+                for (int off = g.T >> 1; off > 0; off >>= 1) acc0 += __shfl_xor_sync(0xffffffffu, acc0, off);
+                if (part == 0 && va) out[row0 + ra] = acc0;
+            }
+        } else {
+            for (int i = 0; i < iters; ++i) {
+                const int ra = rt + i * g.R;
+                const bool va = row0 + ra < g.nact;
+                float acc = 0.f;
+                if (va) {
+#pragma unroll 4
+                    for (int k = part; k < nunits; k += g.T) {
+                        float r[EPU];
+                        load_unit<EPU>(sv + k * EPU, r);
+                        acc = unit_dot<DT, U>(acc, stage + ra * rb + k * U, r);
+                    }
+                }
+                for (int off = g.T >> 1; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+                if (part == 0 && va) out[row0 + ra] = acc;
+            }
+        }
         __syncwarp();
         if (lane == 0) mbar_arrive(smem_addr(&sh.empty_bar[st]));
     }
@@ -466,15 +576,24 @@ __device__ __forceinline__ int consume_slice(const Args& g, const Plan& pl, Shar
 
 // The consumer warps: every tile of the block's slices, one partial vector per
 // slice (partial[s][row] = the row's dot product with the slice's slopes, in unit
-// order).  tile0: the running tile count at entry; returns the count at exit.
+// order).  tile0: the running tile count at entry; returns the count at exit.  The
+// next slice's layout is fetched while the present one is consumed.
 template <int DT>
 __device__ __forceinline__ int consume(const Args& g, const Plan& pl, Shared& sh, int tid, int tile0) {
     int tile = tile0;
+    int rb = pl.rb0, lo = 0;
     for (int s = pl.sb0; s < pl.sb1; ++s) {
-        const int u = row_unit(g.sl.rowbytes[s]);
-        if (u == 16) tile = consume_slice<DT, 16>(g, pl, sh, tid, tile, s);
-        else if (u == 8) tile = consume_slice<DT, 8>(g, pl, sh, tid, tile, s);
-        else tile = consume_slice<DT, 4>(g, pl, sh, tid, tile, s);
+        int rb_next = 0, lo_next = 0;
+        if (s + 1 < pl.sb1) {
+            rb_next = __ldg(g.sl.rowbytes + s + 1);
+            lo_next = __ldg(g.sl.loc + s + 1) - pl.loc0;
+        }
+        const int u = row_unit(rb);
+        if (u == 16) tile = consume_slice<DT, 16>(g, pl, sh, tid, tile, s, rb, lo);
+        else if (u == 8) tile = consume_slice<DT, 8>(g, pl, sh, tid, tile, s, rb, lo);
+        else tile = consume_slice<DT, 4>(g, pl, sh, tid, tile, s, rb, lo);
+        rb = rb_next;
+        lo = lo_next;
     }
     return tile;
 }
@@ -513,8 +632,9 @@ __device__ __forceinline__ void reduce_rows(const Args& g, const Plan& pl, int t
             for (int width = 1; width < kConsumerWarps; width <<= 1)
 #pragma unroll
                 for (int i = 0; i + width < kConsumerWarps; i += 2 * width) t[i] += t[i + width];
-            integrate_row<DT>(row, t[0], pl.a_pre[row - pl.r0], pl.sc_pre[row - pl.r0], g.a, dm_out,
-                              g.gain, g.leak);
+            // the shared copy of the state stays current for a persistent kernel
+            pl.a_pre[row - pl.r0] = integrate_row<DT>(row, t[0], pl.a_pre[row - pl.r0], pl.sc_pre[row - pl.r0],
+                                                      g.a, dm_out, g.gain, g.leak);
         }
         consumer_sync();
     }
@@ -571,12 +691,21 @@ inline Launch plan_launch(const rtc_handle* h, size_t min_region = 0) {
     const size_t extra = L.region + 4 * static_cast<size_t>(L.loc_floats) +
                          8 * static_cast<size_t>(L.row_floats) + 4 * kConsumerWarps * 32;
     const size_t room = kDynSmemBudget > extra ? kDynSmemBudget - extra : 0;
-    // fewest lanes per row for which two stages of R = kConsumers / T rows fit
+    // lanes per row: the fewest for which two stages of R = kConsumers / T rows fit
+    // (splitting rows further to keep the slopes in registers measured slower for
+    // every store type: more tiles and butterflies cost more than the slope reads
+    // they save).  Only the slices decide it, not the block count, so the order of
+    // every row's sum is the same for any launch of the handle.
     auto stage = [&](int T) { return (static_cast<size_t>(kConsumers / T) * max_rb + 15) / 16 * 16; };
     L.T = 1;
     while (L.T < 16 && 2 * stage(L.T) > room) L.T *= 2;      // R stays a multiple of 4
     L.R = kConsumers / L.T;
-    L.stage_bytes = static_cast<int>(stage(L.T));
+    // stages of at least kMinTileBytes (whole multiples of R rows of the widest
+    // slice), so that the per-tile handshakes stay a small part of the work
+    const size_t st1 = stage(L.T);
+    size_t m = st1 > 0 ? std::max<size_t>(1, kMinTileBytes / st1) : 1;
+    while (m > 1 && 2 * m * st1 > room) --m;
+    L.stage_bytes = static_cast<int>(m * st1);
     const size_t fit = L.stage_bytes > 0 ? room / L.stage_bytes : 0;
     L.nst = static_cast<int>(fit < static_cast<size_t>(kMaxStages) ? fit : kMaxStages);
     L.smem = static_cast<size_t>(L.nst) * L.stage_bytes + extra;
@@ -595,6 +724,7 @@ inline Args make_args(const rtc_handle* h, const float* d_s, float* d_dm_out, co
     g.R = L.R;
     g.stage_bytes = L.stage_bytes;
     g.nst = L.nst;
+    g.l2_policy = h->m_bytes <= kL2KeepBytes ? kL2Normal : kL2Stream;
     g.region = static_cast<int>(L.region);
     g.loc_floats = L.loc_floats;
     g.row_floats = L.row_floats;

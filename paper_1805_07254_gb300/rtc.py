@@ -44,7 +44,7 @@ class RtcLoopConfig(C.Structure):
     _fields_ = [("n_frames", C.c_uint64), ("rate_hz", C.c_double), ("source", SOURCE_FN),
                 ("source_user", C.c_void_p), ("preload", C.c_void_p), ("n_preload", C.c_int32),
                 ("sink", SINK_FN), ("sink_user", C.c_void_p), ("e2e_ns", C.c_void_p),
-                ("dev_ns", C.c_void_p)]
+                ("dev_ns", C.c_void_p), ("n_bands", C.c_int32), ("band_interval_us", C.c_double)]
 
 
 class RtcStats(C.Structure):
@@ -66,6 +66,7 @@ SIGNATURES = {
     "rtc_set_threshold": (_I, [_P, C.c_int32, C.c_float]),
     "rtc_load_cmat": (_I, [_P, _P, C.c_int32, C.c_int32, C.c_int32, C.c_int32, _P]),
     "rtc_set_gain": (_I, [_P, C.c_float, C.c_float]),
+    "rtc_set_readout": (_I, [_P, C.c_int32, C.c_double]),
     "rtc_reset": (_I, [_P]),
     "rtc_get_dm": (_I, [_P, _P]),
     "rtc_get_info": (_I, [_P, C.POINTER(RtcInfo)]),
@@ -235,6 +236,12 @@ class Rtc:
     def set_gain(self, gain: float, leak: float):
         self._check(self._lib.rtc_set_gain(self._h, gain, leak))
 
+    def set_readout(self, bands: int, band_interval_us: float = 0.0):
+        """Asymmetric subaperture allocation for a rolling readout of `bands` bands of
+        pixel rows, band_interval_us apart (rtc_set_readout); bands = 0 restores
+        equal slices."""
+        self._check(self._lib.rtc_set_readout(self._h, int(bands), float(band_interval_us)))
+
     def reset(self):
         self._check(self._lib.rtc_reset(self._h))
 
@@ -274,17 +281,21 @@ class Rtc:
                                                     _stream_ptr(stream)))
 
     def run_loop(self, n_frames: int, rate_hz: float = 0.0, frames=None, source=None, sink=None,
-                 record: bool = True):
+                 record: bool = True, bands: int = 0, band_interval_us: float = 0.0):
         """Persistent real-time loop (rtc_run_loop).
 
         frames: uint16 array (n, [n_wfs,] H, W), 1 <= n <= 8, cycled; or source(k) -> frame
         array for frame k (None stops the loop).  sink(k, dm) receives each frame's DM
-        commands (a float32 array valid during the call).  Returns (stats dict, e2e_ns,
-        dev_ns) with per-frame latencies when record is true."""
+        commands (a float32 array valid during the call).  bands > 1 publishes each
+        frame in that many bands of pixel rows, band_interval_us apart (a rolling
+        readout).  Returns (stats dict, e2e_ns, dev_ns) with per-frame latencies when
+        record is true."""
         n_frames = int(n_frames)
         cfg = RtcLoopConfig()
         cfg.n_frames = n_frames
         cfg.rate_hz = float(rate_hz)
+        cfg.n_bands = int(bands)
+        cfg.band_interval_us = float(band_interval_us)
         keep = []
         if source is not None:
             nbytes = [None]

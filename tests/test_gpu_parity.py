@@ -51,7 +51,7 @@ def test_tiny_scao_closed_loop_1000_frames():
 @pytest.mark.parametrize("store", ["f32", "bf16", "f16", "fp8", "int8"])
 def test_launch_plan_slices_and_tiles(store):
     """One slice of consecutive subapertures per SM (fewer if there are fewer
-    subapertures), one block per slice, tiles of 448 / T rows, rings of 2..8 stages;
+    subapertures), one block per slice, tiles of 448 / T rows, rings of 2..32 stages;
     short reduced-precision rows get deeper rings than FP32 rows."""
     cfg = synth.elt_scao()
     r, *_ = make_pair(cfg, store=store)
@@ -60,7 +60,7 @@ def test_launch_plan_slices_and_tiles(store):
     assert info["slices"] == min(sms, cfg.n_valid)
     assert info["blocks"] == info["slices"]
     assert info["tile_rows"] in (448, 224, 112, 56, 28)
-    assert 2 <= info["ring_stages"] <= 8
+    assert 2 <= info["ring_stages"] <= 32
     if store in ("fp8", "int8"):
         r32, *_ = make_pair(cfg, store="f32")
         assert info["ring_stages"] > r32.info()["ring_stages"]
