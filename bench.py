@@ -464,6 +464,28 @@ def ours(args):
                 "dev_p50_us": round(st_l["dev_p50_us"], 2), "dev_p99_us": round(st_l["dev_p99_us"], 2),
                 "dev_rms_jitter_us": round(st_l["dev_rms_jitter_us"], 3)}
             rl.close()
+        # a rolling readout at 1 kHz: 74 bands of 10 pixel rows (one row of
+        # subapertures each), 10 us apart, so the last pixel arrives 730 us after
+        # the first; latency from the last band's publication.  Equal slices, then
+        # the asymmetric allocation for that readout (rtc_set_readout).
+        bands, band_us = cfg.nsub, 10.0
+        for store in ("f32", "bf16", "fp8"):
+            rl = controller(store)
+            for cut in (False, True):
+                if cut:
+                    rl.set_readout(bands, band_us)
+                st_l, _, _ = rl.run_loop(args.loop_frames, rate_hz=1000.0, frames=frames[:8],
+                                         bands=bands, band_interval_us=band_us)
+                loop[f"{store}_1kHz_{bands}bands_{'cut' if cut else 'equal'}"] = {
+                    "frames": int(st_l["frames"]), "slices": rl.info()["slices"],
+                    "band_interval_us": band_us,
+                    "last_pixel_e2e_p50_us": round(st_l["e2e_p50_us"], 2),
+                    "last_pixel_e2e_p99_us": round(st_l["e2e_p99_us"], 2),
+                    "last_pixel_e2e_rms_jitter_us": round(st_l["e2e_rms_jitter_us"], 3),
+                    "last_pixel_dev_p50_us": round(st_l["dev_p50_us"], 2),
+                    "last_pixel_dev_p99_us": round(st_l["dev_p99_us"], 2),
+                    "last_pixel_dev_rms_jitter_us": round(st_l["dev_rms_jitter_us"], 3)}
+            rl.close()
 
     # replicas: the worst replica's latency statistics, the aggregate frames/s
     worst, total_fps = reduce_replicas(torch, dist if world > 1 else None, s_step, dev)

@@ -95,10 +95,14 @@ int dtype_size(int dt) {
 
 // Asymmetric subaperture allocation (Sec. 2.3.3, Fig. 6 (d)): the per-block cost
 // model.  A block that owns n subapertures needs, after the last of their pixel
-// rows has arrived, about n * (2 nact esz / kAllocSmGBs + kAllocPixelNs) ns: its
-// matrix columns streamed by one SM, plus its share of the pixel stage.
-constexpr long long kAllocSmGBs = 60;       // bytes per ns one SM streams
-constexpr long long kAllocPixelNs = 50;
+// rows has arrived, about a + n * 2 nact (esz kAllocPsPerByte + kAllocPsPerElem)
+// ps: the fixed part a is the same for every block and drops out of the cut; the
+// rest is one SM streaming and multiplying the n subapertures' matrix columns.
+// Fitted to ELT blocks running alone on a GB300 SM (506 / 324 / 262 ns per
+// subaperture for FP32 / BF16 / FP8 columns of 4421 rows) and raised by ~1.3x,
+// since blocks of neighbouring bands overlap in time and share the memory system.
+constexpr long long kAllocPsPerByte = 12;
+constexpr long long kAllocPsPerElem = 27;
 constexpr int kAllocMaxWidth = 2;           // largest slice, in mean slice widths
 
 // First subaperture of each slice (the last entry is the subaperture count).
@@ -124,7 +128,7 @@ std::vector<int> slice_bounds(const rtc_handle* h, int esz) {
         t[gi] = band * h->ro_interval_ns;
         t_last = std::max(t_last, t[gi]);
     }
-    const long long c = 2ll * h->cfg.nact * esz / kAllocSmGBs + kAllocPixelNs;
+    const long long c = 2ll * h->cfg.nact * (esz * kAllocPsPerByte + kAllocPsPerElem) / 1000 + 1;
     const int wmax = std::max(1, (kAllocMaxWidth * nt + S - 1) / S);
     auto cut = [&](long long T, std::vector<int>* starts) {
         int p = nt, k = 0;
