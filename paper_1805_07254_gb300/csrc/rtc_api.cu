@@ -79,6 +79,7 @@ void free_slices(rtc_handle* h) {
     h->sl_rowbytes.clear();
     h->sl_g0.clear();
     h->sl_loc.clear();
+    h->sl_equal = false;
     h->m_bytes = 0;
 }
 
@@ -173,6 +174,9 @@ void cut_slices(rtc_handle* h, const std::vector<int>& g0, int esz, std::vector<
     const int nact = h->cfg.nact;
     h->sl_S = S;
     h->sl_g0 = g0;
+    h->sl_equal = true;
+    for (int s = 0; s <= S; ++s)
+        if (g0[s] != static_cast<int>(static_cast<long long>(g0[S]) * s / S)) h->sl_equal = false;
     h->sl_off.resize(S);
     h->sl_rowbytes.resize(S);
     h->sl_loc.resize(S + 1);

@@ -71,6 +71,7 @@ struct rtc_handle {
     std::vector<int> sl_rowbytes;   // [S] bytes per row (multiple of 4)
     std::vector<int> sl_g0;         // [S + 1] first subaperture of each slice
     std::vector<int> sl_loc;        // [S + 1] float offset of each slice's slopes in a local vector
+    bool sl_equal = false;          // sl_g0[s] == nt * s / S for every s
     long long* d_sl_off = nullptr;
     int* d_sl_rowbytes = nullptr;
     int* d_sl_g0 = nullptr;

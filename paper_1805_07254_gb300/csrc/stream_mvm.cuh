@@ -251,6 +251,8 @@ struct Slices {
     const int* g0;           // [S + 1] first subaperture (w * n_valid + i) of slice s
     const int* loc;          // [S + 1] float offset of slice s's slopes in a local vector
     int S;
+    int nt;                  // subapertures over all WFS
+    int equal;               // g0[s] = nt s / S (the default cut): computed, not loaded
 };
 
 struct Args {
@@ -308,11 +310,19 @@ __device__ __forceinline__ Plan make_plan(const Args& g, unsigned char* smem) {
     const int S = g.sl.S;
     pl.sb0 = static_cast<int>(static_cast<long long>(S) * blockIdx.x / gridDim.x);
     pl.sb1 = static_cast<int>(static_cast<long long>(S) * (blockIdx.x + 1) / gridDim.x);
-    pl.g0 = g.sl.g0[pl.sb0];
-    pl.g1 = g.sl.g0[pl.sb1];
+    // the block's subapertures: with the default cut computed, so that the pixel
+    // stage does not wait for a table load before it can fetch positions
+    if (g.sl.equal) {
+        pl.g0 = static_cast<int>(static_cast<long long>(g.sl.nt) * pl.sb0 / S);
+        pl.g1 = static_cast<int>(static_cast<long long>(g.sl.nt) * pl.sb1 / S);
+        pl.n0 = static_cast<int>(static_cast<long long>(g.sl.nt) * (pl.sb0 + 1) / S) - pl.g0;
+    } else {
+        pl.g0 = g.sl.g0[pl.sb0];
+        pl.g1 = g.sl.g0[pl.sb1];
+        pl.n0 = g.sl.g0[pl.sb0 + 1] - pl.g0;
+    }
     // the first slice's layout, read once here rather than on the frame's critical path
     pl.rb0 = g.sl.rowbytes[pl.sb0];
-    pl.n0 = g.sl.g0[pl.sb0 + 1] - pl.g0;
     pl.loc0 = g.sl.loc[pl.sb0];
     pl.r0 = static_cast<int>(static_cast<long long>(g.nact) * blockIdx.x / gridDim.x);
     pl.r1 = static_cast<int>(static_cast<long long>(g.nact) * (blockIdx.x + 1) / gridDim.x);
@@ -718,7 +728,8 @@ inline Launch plan_launch(const rtc_handle* h, size_t min_region = 0) {
 inline Args make_args(const rtc_handle* h, const float* d_s, float* d_dm_out, const Launch& L) {
     Args g{};
     g.M = static_cast<const unsigned char*>(h->d_M);
-    g.sl = Slices{h->d_sl_off, h->d_sl_rowbytes, h->d_sl_g0, h->d_sl_loc, h->sl_S};
+    g.sl = Slices{h->d_sl_off, h->d_sl_rowbytes, h->d_sl_g0, h->d_sl_loc, h->sl_S,
+                  h->sl_S > 0 ? h->sl_g0[h->sl_S] : 0, h->sl_equal ? 1 : 0};
     g.nact = h->cfg.nact;
     g.n_valid = h->n_valid;
     g.T = L.T;
