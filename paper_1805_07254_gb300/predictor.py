@@ -78,6 +78,38 @@ def residuals(S: torch.Tensor, S_hat: torch.Tensor, k0: int = 4) -> tuple[float,
     return pred, lag
 
 
+def train_on(S: torch.Tensor, cfg, steps: int | None = None, batch: int = 4096, lr: float = 1e-3,
+             seed: int = 0, log_every: int = 0):
+    """Train a network on the slope sequence S [frames][2 n_valid] (device) with the
+    library's training kernel: random (subaperture, frame) samples, target the next
+    frame's slope change over sigma = RMS(S).  One epoch of samples unless `steps`
+    is given.  Returns (Mlp, sigma, steps, final loss, seconds)."""
+    dev = S.device
+    n_frames = S.shape[0]
+    sigma = float(torch.sqrt(torch.mean(S ** 2)).item())
+    from synth.mlp_init import init_mlp_params, flatten
+    m = Mlp(device=dev.index or 0, params=flatten(init_mlp_params(seed)))
+    m.set_geometry(cfg.subaps, cfg.nsub)
+    nv = cfg.n_valid
+    if steps is None:
+        steps = max(1, (n_frames - 5) * nv // batch)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(9000 + seed)
+    d_loss = torch.zeros(1, device=dev)
+    samples = torch.empty((batch, 2), dtype=torch.int32, device=dev)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for step in range(steps):
+        samples[:, 0] = torch.randint(0, nv, (batch,), generator=gen, device=dev, dtype=torch.int32)
+        samples[:, 1] = torch.randint(3, n_frames - 1, (batch,), generator=gen, device=dev,
+                                      dtype=torch.int32)
+        m.train_seq(S, samples, sigma, lr, d_loss)
+        if log_every and step % log_every == 0:
+            print(f"step {step} loss {d_loss.item():.5f}", flush=True)
+    torch.cuda.synchronize(dev)
+    return m, sigma, steps, d_loss.item(), time.perf_counter() - t0
+
+
 def train_predictor(cfg=None, train_frames: int = 200_000, test_frames: int = 20_000,
                     steps: int | None = None, batch: int = 4096, lr: float = 1e-3, seed: int = 0,
                     device="cuda:0", log_every: int = 0) -> PredictorResult:
@@ -89,29 +121,7 @@ def train_predictor(cfg=None, train_frames: int = 200_000, test_frames: int = 20
     train_seeds = tuple(1000 + 10 * seed + i for i in range(nl))
     test_seeds = tuple(5000 + 10 * seed + i for i in range(nl))
     S = pipeline_slopes(cfg, train_frames, train_seeds, noise_seed=7000 + seed, device=dev)
-    sigma = float(torch.sqrt(torch.mean(S ** 2)).item())
-    from synth.mlp_init import init_mlp_params, flatten
-    m = Mlp(device=dev.index or 0, params=flatten(init_mlp_params(seed)))
-    m.set_geometry(cfg.subaps, cfg.nsub)
-    nv = cfg.n_valid
-    if steps is None:
-        steps = max(1, (train_frames - 5) * nv // batch)
-    gen = torch.Generator(device=dev)
-    gen.manual_seed(9000 + seed)
-    d_loss = torch.zeros(1, device=dev)
-    samples = torch.empty((batch, 2), dtype=torch.int32, device=dev)
-    torch.cuda.synchronize(dev)
-    t0 = time.perf_counter()
-    for step in range(steps):
-        samples[:, 0] = torch.randint(0, nv, (batch,), generator=gen, device=dev, dtype=torch.int32)
-        samples[:, 1] = torch.randint(3, train_frames - 1, (batch,), generator=gen, device=dev,
-                                      dtype=torch.int32)
-        m.train_seq(S, samples, sigma, lr, d_loss)
-        if log_every and step % log_every == 0:
-            print(f"step {step} loss {d_loss.item():.5f}", flush=True)
-    torch.cuda.synchronize(dev)
-    train_s = time.perf_counter() - t0
-    final_loss = d_loss.item()
+    m, sigma, steps, final_loss, train_s = train_on(S, cfg, steps, batch, lr, seed, log_every)
     del S
     T = pipeline_slopes(cfg, test_frames, test_seeds, noise_seed=8000 + seed, device=dev)
     T_hat = torch.zeros_like(T)
