@@ -87,10 +87,12 @@ class ClosedLoopSim:
         v = v - v.mean()
         return torch.sum(v.double() ** 2)
 
-    def run(self, step, n_frames: int, start: int = 0, burn_in: int = 50, chunk: int = 32) -> LoopScore:
+    def run(self, step, n_frames: int, start: int = 0, burn_in: int = 50, chunk: int = 32,
+            trace: list | None = None) -> LoopScore:
         """Close the loop for frames start .. start+n_frames-1 with `step` (uint16 frame
         (H, W) on the device -> new commands (nact,) on the device, applied from the
-        next frame on).  Scores frames after the first `burn_in`."""
+        next frame on).  Scores frames after the first `burn_in`; `trace` receives each
+        scored frame's residual wavefront RMS (radians) when given."""
         cfg, sh, dev = self.cfg, self.sh, self.device
         nv = cfg.n_valid
         gen = torch.Generator(device=dev)
@@ -110,12 +112,17 @@ class ClosedLoopSim:
                 if c0 + j - start >= burn_in:
                     res_s += torch.sum(s_res.double() ** 2)
                     open_s += torch.sum(s_turb[j].double() ** 2)
-                    res_p += self._phase_sq(ph_turb[j] - self.dm.phase(a)[0])
+                    sq = self._phase_sq(ph_turb[j] - self.dm.phase(a)[0])
+                    res_p += sq
+                    if trace is not None:
+                        trace.append(sq)
                     open_p += self._phase_sq(ph_turb[j])
                     scored += 1
                 frame = sh.render(s_res[None], self.dark[0], self.flat[0], gen)[0]
                 a = step(frame)
         ns = max(scored, 1)
+        if trace is not None:
+            trace[:] = [math.sqrt(v.item() / self.npup) for v in trace]
         return LoopScore(frames=scored,
                          slope_rms_px=math.sqrt(res_s.item() / (ns * 2 * nv)),
                          phase_rms_rad=math.sqrt(res_p.item() / (ns * self.npup)),
@@ -154,7 +161,8 @@ def library_step(r: Rtc, device, slopes: torch.Tensor | None = None):
 
 
 def evaluate(cfg=None, train_frames: int = 20_000, test_frames: int = 5_000, seed: int = 0,
-             store: str = "f32", steps: int | None = None, device="cuda:0") -> dict:
+             store: str = "f32", steps: int | None = None, device="cuda:0",
+             alpha_rel: float = 1e-3) -> dict:
     """Integrator against integrator + predictor in the closed loop.  The predictor
     is trained on the measured residual slopes of an integrator closed loop through
     turbulence with other seeds; both are then scored on the same held-out
@@ -166,7 +174,7 @@ def evaluate(cfg=None, train_frames: int = 20_000, test_frames: int = 5_000, see
     train_seeds = tuple(2000 + 10 * seed + i for i in range(nl))
     test_seeds = tuple(6000 + 10 * seed + i for i in range(nl))
 
-    sim = ClosedLoopSim(cfg, dev, train_seeds, noise_seed=7100 + seed)
+    sim = ClosedLoopSim(cfg, dev, train_seeds, noise_seed=7100 + seed, alpha_rel=alpha_rel)
     r = sim.controller(store)
     S = torch.zeros((train_frames, cfg.nslopes), device=dev)
     train_score = sim.run(library_step(r, dev, slopes=S), train_frames)
@@ -176,7 +184,7 @@ def evaluate(cfg=None, train_frames: int = 20_000, test_frames: int = 5_000, see
     m.close()
     del S
 
-    test = ClosedLoopSim(cfg, dev, test_seeds, noise_seed=8100 + seed)
+    test = ClosedLoopSim(cfg, dev, test_seeds, noise_seed=8100 + seed, alpha_rel=alpha_rel)
     r = test.controller(store)
     integ = test.run(library_step(r, dev), test_frames)
     r.close()
@@ -187,7 +195,7 @@ def evaluate(cfg=None, train_frames: int = 20_000, test_frames: int = 5_000, see
     r.close()
     torch.cuda.synchronize(dev)
     keep = pred.phase_rms_rad < integ.phase_rms_rad
-    return {"config": cfg.name, "store": store, "train_frames": train_frames, "test_frames": test_frames,
+    return {"config": cfg.name, "store": store, "alpha_rel": alpha_rel, "train_frames": train_frames, "test_frames": test_frames,
             "scored_frames": integ.frames, "training_steps": n_steps, "final_loss": loss,
             "train_seconds": round(train_s, 2), "sigma_px": sigma,
             "train_loop_residual_phase_nm": train_score.phase_rms_nm,
@@ -209,9 +217,11 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=None)
     ap.add_argument("--store", default="f32", choices=["f32", "bf16", "f16", "fp8", "int8"])
     ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--alpha", type=float, default=1e-3, help="reconstructor regularisation, "
+                    "relative to the mean diagonal of D^T D")
     a = ap.parse_args(argv)
     print(json.dumps(evaluate(synth.CONFIGS[a.config](), a.train_frames, a.test_frames, a.seed,
-                              a.store, a.steps)))
+                              a.store, a.steps, alpha_rel=a.alpha)))
 
 
 if __name__ == "__main__":
