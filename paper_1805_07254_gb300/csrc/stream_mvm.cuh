@@ -496,18 +496,20 @@ __device__ __forceinline__ int consume_slice(const Args& g, const Plan& pl, Shar
                                              int tile, int s, int rb, int lo) {
     constexpr int EPU = U / Esize<DT>::v;                    // elements per unit
     constexpr int JM = LaneUnits<DT, U>::v;
+    // launch constants in registers for the row loops
+    const int T = g.T, R = g.R, nact = g.nact, nst = g.nst, stage_bytes = g.stage_bytes;
     const int lane = tid & 31;
-    const int rt = tid / g.T;                                // row of the tile
-    const int part = tid - rt * g.T;                         // lane within the row's group
+    const int rt = tid / T;                                  // row of the tile
+    const int part = tid - rt * T;                           // lane within the row's group
     const int nunits = rb / U;
     const float* sv = pl.loc + lo;
-    float* out = g.partial + static_cast<size_t>(s) * g.nact;
+    float* out = g.partial + static_cast<size_t>(s) * nact;
     const int tr = tile_rows(g, rb);
-    const bool in_regs = (nunits + g.T - 1) / g.T <= JM;     // the same for the whole block
+    const bool in_regs = (nunits + T - 1) / T <= JM;     // the same for the whole block
     float sr[JM][EPU];
 #pragma unroll
     for (int j = 0; j < JM; ++j) {
-        const int k = part + j * g.T;
+        const int k = part + j * T;
         if (in_regs && k < nunits) {
             load_unit<EPU>(sv + k * EPU, sr[j]);
         } else {
@@ -515,10 +517,10 @@ __device__ __forceinline__ int consume_slice(const Args& g, const Plan& pl, Shar
             for (int e = 0; e < EPU; ++e) sr[j][e] = 0.f;
         }
     }
-    for (int row0 = 0; row0 < g.nact; row0 += tr, ++tile) {
-        const int st = tile % g.nst;
+    for (int row0 = 0; row0 < nact; row0 += tr, ++tile) {
+        const int st = tile % nst;
         const bool ok = __all_sync(0xffffffffu, wait_phase(smem_addr(&sh.full_bar[st]),
-                                                            (tile / g.nst) & 1, &sh.abort_flag));
+                                                            (tile / nst) & 1, &sh.abort_flag));
         if (!ok) {
             if (lane == 0 && !sh.abort_flag) {
                 atomicExch(g.status, RTC_ETIMEDOUT);
@@ -526,24 +528,24 @@ __device__ __forceinline__ int consume_slice(const Args& g, const Plan& pl, Shar
             }
             continue;     // skip the work but keep reaching the block's barriers
         }
-        const uint32_t stage = pl.ring + st * g.stage_bytes;
+        const uint32_t stage = pl.ring + st * stage_bytes;
         // rows of this tile per lane group: the same count on every lane
-        const int iters = (min(tr, g.nact - row0) + g.R - 1) / g.R;
+        const int iters = (min(tr, nact - row0) + R - 1) / R;
         if (in_regs) {
             int i = 0;
             for (; i + 2 <= iters; i += 2) {                 // two rows in flight
-                const int ra = rt + i * g.R, rbw = ra + g.R;
-                const bool va = row0 + ra < g.nact, vb = row0 + rbw < g.nact;
+                const int ra = rt + i * R, rbw = ra + R;
+                const bool va = row0 + ra < nact, vb = row0 + rbw < nact;
                 float acc0 = 0.f, acc1 = 0.f;
 #pragma unroll
                 for (int j = 0; j < JM; ++j) {
-                    const int k = part + j * g.T;
+                    const int k = part + j * T;
                     if (k < nunits) {
                         if (va) acc0 = unit_dot<DT, U>(acc0, stage + ra * rb + k * U, sr[j]);
                         if (vb) acc1 = unit_dot<DT, U>(acc1, stage + rbw * rb + k * U, sr[j]);
                     }
                 }
-                for (int off = g.T >> 1; off > 0; off >>= 1) {
+                for (int off = T >> 1; off > 0; off >>= 1) {
                     acc0 += __shfl_xor_sync(0xffffffffu, acc0, off);
                     acc1 += __shfl_xor_sync(0xffffffffu, acc1, off);
                 }
@@ -551,31 +553,31 @@ __device__ __forceinline__ int consume_slice(const Args& g, const Plan& pl, Shar
                 if (part == 0 && vb) out[row0 + rbw] = acc1;
             }
             if (i < iters) {
-                const int ra = rt + i * g.R;
-                const bool va = row0 + ra < g.nact;
+                const int ra = rt + i * R;
+                const bool va = row0 + ra < nact;
                 float acc0 = 0.f;
 #pragma unroll
                 for (int j = 0; j < JM; ++j) {
-                    const int k = part + j * g.T;
+                    const int k = part + j * T;
                     if (k < nunits && va) acc0 = unit_dot<DT, U>(acc0, stage + ra * rb + k * U, sr[j]);
                 }
-                for (int off = g.T >> 1; off > 0; off >>= 1) acc0 += __shfl_xor_sync(0xffffffffu, acc0, off);
+                for (int off = T >> 1; off > 0; off >>= 1) acc0 += __shfl_xor_sync(0xffffffffu, acc0, off);
                 if (part == 0 && va) out[row0 + ra] = acc0;
             }
         } else {
             for (int i = 0; i < iters; ++i) {
-                const int ra = rt + i * g.R;
-                const bool va = row0 + ra < g.nact;
+                const int ra = rt + i * R;
+                const bool va = row0 + ra < nact;
                 float acc = 0.f;
                 if (va) {
 #pragma unroll 4
-                    for (int k = part; k < nunits; k += g.T) {
+                    for (int k = part; k < nunits; k += T) {
                         float r[EPU];
                         load_unit<EPU>(sv + k * EPU, r);
                         acc = unit_dot<DT, U>(acc, stage + ra * rb + k * U, r);
                     }
                 }
-                for (int off = g.T >> 1; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+                for (int off = T >> 1; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
                 if (part == 0 && va) out[row0 + ra] = acc;
             }
         }
