@@ -207,6 +207,36 @@ int rtc_synchronize(rtc_handle* h, void* stream);
  * unloaded). */
 int rtc_set_readout(rtc_handle* h, int32_t n_bands, double band_interval_us);
 
+/* ---- planning helpers (host only) ------------------------------------------
+ * What rtc_set_readout and rtc_run_loop work out on the host, without a handle or
+ * a device, for inspection and tests.  rc: int32 [n_valid][2] (row, col) grid
+ * positions of one WFS's valid subapertures, as for rtc_load_subaps; with n_wfs
+ * WFS the subapertures are numbered WFS by WFS (gi = w * n_valid + i). */
+
+/* The slice cut: g0_out[0 .. *n_slices] receives the first subaperture of each of
+ * at most max_slices slices of consecutive subapertures, then their count.  With
+ * n_bands <= 1 the slices are equal; otherwise the asymmetric cut of
+ * rtc_set_readout for n_bands bands band_interval_us apart, with the cost model
+ * of a `store` (rtc_dtype) matrix of nact rows.  g0_out holds max_slices + 1
+ * entries.  Errors: RTC_EINVAL. */
+int rtc_plan_slices(const int32_t* rc, int32_t n_valid, int32_t n_wfs, int32_t nsub, int32_t npx,
+                    int32_t nact, int32_t store, int32_t max_slices, int32_t n_bands,
+                    double band_interval_us, int32_t* g0_out, int32_t* n_slices);
+
+/* The persistent loop's ingest table for `blocks` blocks over the slices g0[0 ..
+ * n_slices] (block b takes slices n_slices*b/blocks .. n_slices*(b+1)/blocks - 1):
+ * blk_out[4b .. 4b+3] = {first unit, end unit, band that completes the block, 0}
+ * and units_out[first .. end) the block's copy units, sorted and distinct: frame
+ * byte offset / unit_bytes (2, 4 or 16) of every unit that the pixel rows of its
+ * subapertures touch, the frame being uint16 [n_wfs][H][W], H = W = nsub * npx.
+ * *n_units receives the total; units_out may be NULL to ask for it, else it holds
+ * units_cap entries.  Errors: RTC_EINVAL (bad geometry, slices that are empty or
+ * do not cover 0 .. n_wfs * n_valid, units_cap too small). */
+int rtc_plan_ingest(const int32_t* rc, int32_t n_valid, int32_t n_wfs, int32_t nsub, int32_t npx,
+                    const int32_t* g0, int32_t n_slices, int32_t blocks, int32_t unit_bytes,
+                    int32_t n_bands, int32_t* blk_out, uint32_t* units_out, int64_t units_cap,
+                    int64_t* n_units);
+
 /* ---- persistent real-time loop ---------------------------------------------
  * The paper's RTC runs its threads continuously and hands work over through
  * spinning on flags rather than sleeping (Sec. 2.3.2); latency is measured from

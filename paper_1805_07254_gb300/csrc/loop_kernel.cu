@@ -275,43 +275,17 @@ cudaError_t launch_t(const Launch& Lc, LoopArgs a, cudaStream_t st) {
                                        dim3(Lc.G), dim3(kThreads), args, Lc.smem, st);
 }
 
-// The copy units and the completing band of every block of a G-block launch: for
-// each run of the block's subapertures that are neighbours in one row of the
-// subaperture grid, the units that the run's pixel rows cover; sorted and without
-// repeats, so that neighbouring threads read neighbouring units.
+// The copy units and the completing band of every block of a G-block launch
+// (plan_ingest: for each run of the block's subapertures that are neighbours in
+// one row of the subaperture grid, the units its pixel rows cover; sorted and
+// without repeats, so that neighbouring threads read neighbouring units).
 int build_ingest(rtc_handle* h, int G, int unit, int n_bands) {
-    const int S = h->sl_S, nv = h->n_valid, npx = h->cfg.npx, side = h->side;
     std::vector<unsigned> units;
+    std::vector<int> b4;
+    plan_ingest(h->rc.data(), h->n_valid, h->cfg.npx, h->side, h->sl_g0.data(), h->sl_S, G, unit, n_bands,
+                units, b4);
     std::vector<int4> blk(G);
-    std::vector<unsigned> mine;
-    for (int b = 0; b < G; ++b) {
-        const int g0 = h->sl_g0[static_cast<long long>(S) * b / G];
-        const int g1 = h->sl_g0[static_cast<long long>(S) * (b + 1) / G];
-        mine.clear();
-        int last_row = 0;
-        for (int gi = g0; gi < g1;) {
-            const int w = gi / nv, i = gi - w * nv;
-            const int r = h->rc[2 * i], c = h->rc[2 * i + 1];
-            int n = 1;
-            while (gi + n < g1 && (gi + n) / nv == w && h->rc[2 * (i + n)] == r &&
-                   h->rc[2 * (i + n) + 1] == c + n)
-                ++n;
-            for (int y = 0; y < npx; ++y) {
-                const long long row = static_cast<long long>(w) * side + static_cast<long long>(r) * npx + y;
-                const long long b0 = (row * side + static_cast<long long>(c) * npx) * 2;
-                const long long b1 = b0 + static_cast<long long>(n) * npx * 2;
-                for (long long u = b0 / unit; u <= (b1 - 1) / unit; ++u) mine.push_back(static_cast<unsigned>(u));
-            }
-            last_row = std::max(last_row, r * npx + npx - 1);
-            gi += n;
-        }
-        std::sort(mine.begin(), mine.end());
-        mine.erase(std::unique(mine.begin(), mine.end()), mine.end());
-        // row y belongs to band j when floor(side j / n) <= y < floor(side (j+1) / n)
-        const int band = static_cast<int>(((static_cast<long long>(last_row) + 1) * n_bands - 1) / side);
-        blk[b] = make_int4(static_cast<int>(units.size()), static_cast<int>(units.size() + mine.size()), band, 0);
-        units.insert(units.end(), mine.begin(), mine.end());
-    }
+    for (int b = 0; b < G; ++b) blk[b] = make_int4(b4[4 * b], b4[4 * b + 1], b4[4 * b + 2], 0);
     if (units.empty()) units.push_back(0);
     if (units.size() > h->units_cap) {
         if (h->d_units) cudaFree(h->d_units);

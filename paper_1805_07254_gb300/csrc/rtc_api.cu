@@ -94,74 +94,10 @@ int dtype_size(int dt) {
     }
 }
 
-// Asymmetric subaperture allocation (Sec. 2.3.3, Fig. 6 (d)): the per-block cost
-// model.  A block that owns n subapertures needs, after the last of their pixel
-// rows has arrived, about a + n * 2 nact (esz kAllocPsPerByte + kAllocPsPerElem)
-// ps: the fixed part a is the same for every block and drops out of the cut; the
-// rest is one SM streaming and multiplying the n subapertures' matrix columns.
-// Fitted to ELT blocks running alone on a GB300 SM (506 / 324 / 262 ns per
-// subaperture for FP32 / BF16 / FP8 columns of 4421 rows) and raised by ~1.3x,
-// since blocks of neighbouring bands overlap in time and share the memory system.
-constexpr long long kAllocPsPerByte = 12;
-constexpr long long kAllocPsPerElem = 27;
-constexpr int kAllocMaxWidth = 2;           // largest slice, in mean slice widths
-
-// First subaperture of each slice (the last entry is the subaperture count).
-// Without a readout model: equal slices of consecutive subapertures, one per SM.
-// With one (n_bands bands of pixel rows, interval_ns apart): the cut that lets
-// every slice finish by the earliest common time T, found by bisection on T; for
-// a given T the slices are cut from the end of the subaperture order, each as
-// long as the latest arrival among its subapertures plus its cost stays within T
-// (and within kAllocMaxWidth mean widths), so that the subapertures of the last
-// rows get slices of their own and those that arrive early share large ones.
+// First subaperture of each slice for the handle's readout model (plan.cu).
 std::vector<int> slice_bounds(const rtc_handle* h, int esz) {
-    const int nt = h->n_valid * h->cfg.n_wfs;
-    const int S = std::min(h->dev_sms, nt);
-    std::vector<int> g0(S + 1);
-    for (int s = 0; s <= S; ++s) g0[s] = static_cast<int>(static_cast<long long>(nt) * s / S);
-    if (h->ro_bands <= 1 || nt <= S) return g0;
-    const int nv = h->n_valid, npx = h->cfg.npx, side = h->side, nb = h->ro_bands;
-    std::vector<long long> t(nt);
-    long long t_last = 0;
-    for (int gi = 0; gi < nt; ++gi) {
-        const int i = gi % nv;
-        const long long band = ((static_cast<long long>(h->rc[2 * i]) * npx + npx) * nb - 1) / side;
-        t[gi] = band * h->ro_interval_ns;
-        t_last = std::max(t_last, t[gi]);
-    }
-    const long long c = 2ll * h->cfg.nact * (esz * kAllocPsPerByte + kAllocPsPerElem) / 1000 + 1;
-    const int wmax = std::max(1, (kAllocMaxWidth * nt + S - 1) / S);
-    auto cut = [&](long long T, std::vector<int>* starts) {
-        int p = nt, k = 0;
-        while (p > 0) {
-            int n = 0;
-            long long tmax = 0;
-            while (p - n > 0 && n < wmax) {
-                const long long tm = std::max(tmax, t[p - n - 1]);
-                if (n > 0 && tm + c * (n + 1) > T) break;
-                tmax = tm;
-                ++n;
-            }
-            p -= n;
-            ++k;
-            if (starts) starts->push_back(p);
-        }
-        return k;
-    };
-    long long lo = t_last + c, hi = t_last + c * nt;   // cut(hi) <= ceil(nt / wmax) <= S
-    if (cut(lo, nullptr) > S) {
-        while (hi - lo > 1) {
-            const long long mid = lo + (hi - lo) / 2;
-            if (cut(mid, nullptr) <= S) hi = mid;
-            else lo = mid;
-        }
-        lo = hi;
-    }
-    std::vector<int> starts;
-    cut(lo, &starts);
-    std::reverse(starts.begin(), starts.end());
-    starts.push_back(nt);
-    return starts;
+    return plan_slices(h->rc.data(), h->n_valid, h->cfg.n_wfs, h->cfg.npx, h->side, h->cfg.nact, esz,
+                       h->dev_sms, h->ro_bands, h->ro_interval_ns);
 }
 
 // The slice table for slice bounds g0, in the handle's host vectors: each slice one

@@ -170,6 +170,15 @@ bool rtc_handle_ready(const rtc_handle* h);
 int64_t rtc_handle_device_bytes(const rtc_handle* h);
 int fail_handle(rtc_handle* h, int code, const char* msg);
 
+// Host planning (plan.cu).  plan_slices: first subaperture of each slice (then
+// the subaperture count): equal slices, or with n_bands > 1 the asymmetric cut
+// for that readout.  plan_ingest: the persistent loop's per-block copy units and
+// completing band (blk: 4 ints per block) for G blocks over slices g0[0..S].
+std::vector<int> plan_slices(const int32_t* rc, int nv, int nw, int npx, int side, int nact, int esz,
+                             int max_slices, int n_bands, long long interval_ns);
+void plan_ingest(const int32_t* rc, int nv, int npx, int side, const int* g0, int S, int G, int unit,
+                 int n_bands, std::vector<unsigned>& units, std::vector<int>& blk);
+
 // While a persistent loop runs, a release (rtc_destroy, rtc_mlp_destroy,
 // rtc_server_destroy) would wait for the device and so for the loop, whose kernel
 // in turn waits for frames from the host thread: called from a source or sink

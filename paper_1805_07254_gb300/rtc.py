@@ -67,6 +67,10 @@ SIGNATURES = {
     "rtc_load_cmat": (_I, [_P, _P, C.c_int32, C.c_int32, C.c_int32, C.c_int32, _P]),
     "rtc_set_gain": (_I, [_P, C.c_float, C.c_float]),
     "rtc_set_readout": (_I, [_P, C.c_int32, C.c_double]),
+    "rtc_plan_slices": (_I, [_P, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_int32,
+                             C.c_int32, C.c_int32, C.c_double, _P, _P]),
+    "rtc_plan_ingest": (_I, [_P, C.c_int32, C.c_int32, C.c_int32, C.c_int32, _P, C.c_int32, C.c_int32,
+                             C.c_int32, C.c_int32, _P, _P, C.c_int64, _P]),
     "rtc_reset": (_I, [_P]),
     "rtc_get_dm": (_I, [_P, _P]),
     "rtc_get_info": (_I, [_P, C.POINTER(RtcInfo)]),
@@ -499,3 +503,39 @@ class Mlp:
 
 def version() -> str:
     return load_library().rtc_version().decode()
+
+
+def plan_slices(rc, nsub: int, npx: int, nact: int, store: str = "f32", max_slices: int = 152,
+                bands: int = 0, band_interval_us: float = 0.0, n_wfs: int = 1) -> np.ndarray:
+    """The slice cut (rtc_plan_slices): first subaperture of each slice, then the
+    subaperture count.  Host only."""
+    lib = load_library()
+    rc = np.ascontiguousarray(rc, dtype=np.int32).reshape(-1, 2)
+    g0 = np.zeros(max_slices + 1, np.int32)
+    n = C.c_int32(0)
+    rc_ = lib.rtc_plan_slices(_ptr(rc), rc.shape[0], n_wfs, nsub, npx, nact, DTYPES[store], max_slices,
+                              int(bands), float(band_interval_us), _ptr(g0), C.byref(n))
+    if rc_ != RTC_OK:
+        raise RtcError(rc_, "rtc_plan_slices rejected its arguments")
+    return g0[:n.value + 1].copy()
+
+
+def plan_ingest(rc, nsub: int, npx: int, g0, blocks: int, unit_bytes: int = 16, bands: int = 1,
+                n_wfs: int = 1):
+    """The persistent loop's ingest table (rtc_plan_ingest): (blk [blocks][4] int32,
+    units uint32).  Host only."""
+    lib = load_library()
+    rc = np.ascontiguousarray(rc, dtype=np.int32).reshape(-1, 2)
+    g0 = np.ascontiguousarray(g0, dtype=np.int32)
+    blk = np.zeros((blocks, 4), np.int32)
+    n = C.c_int64(0)
+    args = (_ptr(rc), rc.shape[0], n_wfs, nsub, npx, _ptr(g0), g0.shape[0] - 1, blocks, unit_bytes, int(bands),
+            _ptr(blk))
+    rc_ = lib.rtc_plan_ingest(*args, None, 0, C.byref(n))
+    if rc_ != RTC_OK:
+        raise RtcError(rc_, "rtc_plan_ingest rejected its arguments")
+    units = np.zeros(max(n.value, 1), np.uint32)
+    rc_ = lib.rtc_plan_ingest(*args, _ptr(units), units.shape[0], C.byref(n))
+    if rc_ != RTC_OK:
+        raise RtcError(rc_, "rtc_plan_ingest rejected its arguments")
+    return blk, units[:n.value]
