@@ -277,6 +277,30 @@ def time_steps(torch, r, d_frames, d_dm, flush, st, n_steps, n_warm, fused=True)
     return cog, mvm, step
 
 
+def launch_floor(torch, flush, st, n_steps, n_warm=20):
+    """Event time (us, p50) of one trivial kernel (a 1-element add) timed exactly
+    like a frame: after the same L2 flush, between two events on st, queued behind
+    a device sleep.  Every per-launch time above contains this much launch cost."""
+    E = torch.cuda.Event
+    tiny = torch.zeros(1, device=flush.device)
+    flush_out = torch.empty((), dtype=flush.dtype, device=flush.device)
+    with torch.cuda.stream(st):
+        for _ in range(n_warm):
+            torch.sum(flush, dim=0, out=flush_out)
+            tiny.add_(1.0)
+        st.synchronize()
+        evs = [(E(enable_timing=True), E(enable_timing=True)) for _ in range(n_steps)]
+        for b0 in range(0, n_steps, BATCH):
+            torch.cuda._sleep(int(2e6))
+            for i in range(b0, min(b0 + BATCH, n_steps)):
+                torch.sum(flush, dim=0, out=flush_out)
+                evs[i][0].record(st)
+                tiny.add_(1.0)
+                evs[i][1].record(st)
+        st.synchronize()
+    return pct([a.elapsed_time(b) * 1e3 for a, b in evs], 0.5)
+
+
 REPLICA_STATS = ("p50", "p99", "p999", "rms_jitter", "peak_to_peak", "mean")
 
 
@@ -499,6 +523,7 @@ def ours(args):
                          f"time-bounded at {args.cpu_sample_s:.0f} s); p50 per frame"}
 
     traffic = recorded_traffic(f"elt_{args.store}")
+    floor_us = launch_floor(torch, flush, st, min(args.steps, 1000))
     line = {
         "metric": METRIC, "value": round(value, 3), "unit": "us", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup,
@@ -516,7 +541,8 @@ def ours(args):
         "roofline": {"kernel": "frame_kernel", "bound": "hbm", "achieved": round(frame_gbs, 1),
                      "peak": hbm_peak, "peak_kind": peak_kind, "unit": "GB/s",
                      "frac": round(frame_gbs / hbm_peak, 4), "traffic": traffic,
-                     "algorithmic_bytes": step_bytes},
+                     "algorithmic_bytes": step_bytes,
+                     "launch_floor_us": round(floor_us, 3)},
         "e2e": {"value": round(s_e2e["p50"], 3), "unit": "us", "p99_us": round(s_e2e["p99"], 3),
                 "rms_jitter_us": round(s_e2e["rms_jitter"], 3),
                 "h2d_bytes_per_step": info["frame_bytes"], "d2h_bytes_per_step": 4 * cfg.nact,
