@@ -6,7 +6,7 @@ library's own forward/backward/Adam kernels (rtc_mlp_train_seq) on random
 (subaperture, frame) samples; evaluation runs rtc_mlp_predict_seq on held-out
 frames from new seeds.
 
-The judge of the predictor is the plain integrator's one-frame servo lag:
+The yardstick for the predictor is the plain integrator's one-frame servo lag:
   integrator residual = RMS(s_{k+1} - s_k)       (commands built from s_k act on k+1)
   predictor residual  = RMS(s_{k+1} - s_hat_{k+1})
 over the same held-out frames.  The predictor is kept only if its residual is
