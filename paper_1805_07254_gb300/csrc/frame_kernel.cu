@@ -88,13 +88,16 @@ frame_kernel(rtc_pixel::PixelArgs px, Args g, rtc_pred::PredArgs pa, int head,
     unsigned long long next = target;   // arrivals that complete the next grid barrier
     if (PRED) {
         // every block's measured slopes in the history ring, then the prediction of
-        // the block's own subapertures, which replaces their local slopes
+        // the block's own subapertures, which replaces their local slopes; the
+        // network's registers are fetched while the barrier waits
+        rtc_pred::Regs pr;
+        rtc_pred::prefetch(pa, tid, pl.g0, pl.g1, pr);
         consumer_sync();
         if (tid == 0) grid_barrier(gridbar, next, g.status, &sh.abort_flag);
         consumer_sync();
         next += gridDim.x;
         if (!sh.abort_flag) {
-            rtc_pred::predict(pa, pl.scratch, tid, pl.g0, pl.g1, head);
+            rtc_pred::predict(pa, pl.scratch, tid, pl.g0, pl.g1, head, pr);
             gather_local(g, pl, tid, pa.s_pred, true);
         }
     }

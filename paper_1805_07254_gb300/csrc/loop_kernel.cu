@@ -232,11 +232,13 @@ __global__ void __launch_bounds__(kThreads, 1) loop_kernel(LoopArgs L) {
         // 3. with the predictor: every block's measured slopes in the history ring,
         //    then the prediction of the block's own subapertures
         if (PRED) {
+            rtc_pred::Regs pr;
+            rtc_pred::prefetch(L.pa, tid, pl.g0, pl.g1, pr);   // overlaps the barrier's wait
             consumer_sync();
             if (tid == 0) grid_barrier(L.gridbar, G * (kBarriers * k + 1), L.mv.status, &sh.abort_flag);
             consumer_sync();
             if (sh.abort_flag) break;
-            rtc_pred::predict(L.pa, pl.scratch, tid, pl.g0, pl.g1, head);
+            rtc_pred::predict(L.pa, pl.scratch, tid, pl.g0, pl.g1, head, pr);
             gather_local(L.mv, pl, tid, L.pa.s_pred, true);
         }
         consumer_sync();

@@ -130,12 +130,11 @@ __device__ __forceinline__ void prefetch(const PredArgs& pa, int tid, int i0, in
 
 // After the grid barrier that completes the measured slopes: predictions of
 // subapertures [i0, i1) from the ring rows head, head-1, head-2, head-3 (newest
-// first).  Every consumer thread calls it; sm is TS-sample scratch of kSmemBytes.
-// Ends with a consumer barrier.
+// first), with the registers `prefetch` filled (before the barrier, so that the
+// weight and neighbour loads overlap the wait).  Every consumer thread calls it;
+// sm is TS-sample scratch of kSmemBytes.  Ends with a consumer barrier.
 __device__ __forceinline__ void predict(const PredArgs& pa, unsigned char* sm, int tid, int i0, int i1,
-                                        int head) {
-    Regs r;
-    prefetch(pa, tid, i0, i1, r);
+                                        int head, const Regs& r) {
     const int warp = tid >> 5, lane = tid & 31;
     const int g = lane >> 2, t = lane & 3;
     __nv_bfloat16* X = reinterpret_cast<__nv_bfloat16*>(sm + SM_X);
