@@ -272,8 +272,10 @@ typedef struct rtc_loop_config {
     int32_t n_preload;           /* 1 .. RTC_LOOP_SLOTS */
     rtc_dm_sink sink;            /* or NULL */
     void* sink_user;
-    int64_t* e2e_ns;             /* [n_frames] publish -> DM visible on the host, or NULL */
-    int64_t* dev_ns;             /* [n_frames] frame seen -> DM written, device clock, or NULL */
+    int64_t* e2e_ns;             /* [n_frames] publication (of the last band) -> DM visible
+                                    on the host, or NULL */
+    int64_t* dev_ns;             /* [n_frames] the last block has its pixel rows -> DM
+                                    written, device clock, or NULL */
     int32_t n_bands;             /* 0 or 1: each frame is published whole.  2 .. H: in
                                     n_bands bands of pixel rows, top to bottom, as a
                                     rolling-shutter camera reads out; band j holds rows

@@ -21,7 +21,7 @@ constexpr int kMaxKsplit = 32;
 // Completion record of one loop frame, written by the device into mapped host memory.
 struct rtc_loop_done {
     unsigned long long seq;      // k + 1 once frame k's DM commands are in host memory
-    unsigned long long t_seen;   // device %globaltimer when the frame's flag was seen
+    unsigned long long t_seen;   // device %globaltimer: the latest time a block had its pixel rows
     unsigned long long t_done;   // device %globaltimer when the last block finished
     unsigned long long pad;
 };
