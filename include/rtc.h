@@ -106,7 +106,8 @@ const char* rtc_last_error(const rtc_handle* h);
  * Errors: RTC_EINVAL (bad geometry or parameters), RTC_ENOMEM, RTC_EDEVICE. */
 int rtc_create(const rtc_config* cfg, rtc_handle** out);
 
-/* Release everything the handle owns.  NULL is accepted.  Called while any
+/* Release everything the handle owns.  NULL is accepted.  RTC_ESTATE while the
+ * handle's job is in a server slot (rtc_slot_submit).  Called while any
  * rtc_run_loop is running (from its callbacks, or from another thread), the
  * release is queued and carried out when the last running loop returns: freeing
  * device memory waits for the device, which would wait for the loop. */
@@ -330,7 +331,8 @@ int rtc_server_destroy(rtc_server* s);
 /* Admit a job: frames host uint16 [n_frames][n_wfs][H][W] (pinned memory keeps the
  * submission asynchronous), dm_out host float32 [n_frames][nact] receives each
  * frame's DM commands.  Both stay owned by the caller and must stay valid until
- * rtc_slot_poll reports the job done; the handle must not be used meanwhile.
+ * rtc_slot_poll reports the job done; meanwhile the handle's own calls (rtc_destroy
+ * included) return RTC_ESTATE, since the job's kernels use its device state.
  * *slot receives the slot id.  Errors: RTC_EINVAL, RTC_ESTATE (handle not ready
  * or already in a slot, or on another device), RTC_EBUSY (no slot or not enough
  * memory budget now), RTC_EDEVICE. */

@@ -375,6 +375,7 @@ int rtc_create(const rtc_config* cfg, rtc_handle** out) {
 
 int rtc_destroy(rtc_handle* h) {
     if (!h) return RTC_OK;
+    if (h->in_slot.load()) return fail(h, RTC_ESTATE, "the handle's job is in a server slot");
     if (release_or_defer([h] { rtc_destroy(h); })) return RTC_OK;
     DeviceScope ds(h->cfg.device);
     if (h->stream) cudaStreamSynchronize(h->stream);
@@ -409,6 +410,7 @@ int rtc_destroy(rtc_handle* h) {
 
 int rtc_load_subaps(rtc_handle* h, const int32_t* rc, int32_t n_valid) {
     if (!h) return RTC_EINVAL;
+    if (h->in_slot.load()) return fail(h, RTC_ESTATE, "the handle's job is in a server slot");
     if (n_valid < 0 || (n_valid > 0 && !rc)) return fail(h, RTC_EINVAL, "bad subap map");
     DeviceScope ds(h->cfg.device);
     RTC_CUDA(h, cudaStreamSynchronize(h->stream));
@@ -418,6 +420,7 @@ int rtc_load_subaps(rtc_handle* h, const int32_t* rc, int32_t n_valid) {
 
 int rtc_load_calib(rtc_handle* h, const float* dark, const float* flat, int64_t npix) {
     if (!h) return RTC_EINVAL;
+    if (h->in_slot.load()) return fail(h, RTC_ESTATE, "the handle's job is in a server slot");
     const int side = h->side, npx = h->cfg.npx, nw = h->cfg.n_wfs, nv = h->n_valid;
     const int64_t want = static_cast<int64_t>(nw) * side * side;
     if (!dark || !flat || npix != want)
@@ -456,6 +459,7 @@ int rtc_load_calib(rtc_handle* h, const float* dark, const float* flat, int64_t 
 
 int rtc_set_threshold(rtc_handle* h, int32_t mode, float thr) {
     if (!h) return RTC_EINVAL;
+    if (h->in_slot.load()) return fail(h, RTC_ESTATE, "the handle's job is in a server slot");
     if ((mode != 0 && mode != 1) || !isfinite(thr)) return fail(h, RTC_EINVAL, "bad threshold");
     h->thr_mode = mode;
     h->thr = thr;
@@ -465,6 +469,7 @@ int rtc_set_threshold(rtc_handle* h, int32_t mode, float thr) {
 int rtc_load_cmat(rtc_handle* h, const void* M, int32_t nact, int32_t nslopes, int32_t src,
                   int32_t store, const float* row_scales) {
     if (!h) return RTC_EINVAL;
+    if (h->in_slot.load()) return fail(h, RTC_ESTATE, "the handle's job is in a server slot");
     if (!M) return fail(h, RTC_EINVAL, "M is NULL");
     if (nact != h->cfg.nact || nslopes != h->nslopes)
         return fail(h, RTC_EINVAL, "matrix is %dx%d, handle expects %dx%d", nact, nslopes, h->cfg.nact, h->nslopes);
@@ -522,6 +527,7 @@ int rtc_load_cmat(rtc_handle* h, const void* M, int32_t nact, int32_t nslopes, i
 
 int rtc_set_readout(rtc_handle* h, int32_t n_bands, double band_interval_us) {
     if (!h) return RTC_EINVAL;
+    if (h->in_slot.load()) return fail(h, RTC_ESTATE, "the handle's job is in a server slot");
     if (n_bands < 0 || n_bands > h->side || !(band_interval_us >= 0.0) || !(band_interval_us <= 1e6))
         return fail(h, RTC_EINVAL, "n_bands must be 0 .. frame height and band_interval_us in [0, 1e6]");
     DeviceScope ds(h->cfg.device);
@@ -577,6 +583,7 @@ int rtc_set_readout(rtc_handle* h, int32_t n_bands, double band_interval_us) {
 
 int rtc_set_gain(rtc_handle* h, float gain, float leak) {
     if (!h) return RTC_EINVAL;
+    if (h->in_slot.load()) return fail(h, RTC_ESTATE, "the handle's job is in a server slot");
     if (!isfinite(gain) || !isfinite(leak)) return fail(h, RTC_EINVAL, "gain and leak must be finite");
     h->gain = gain;
     h->leak = leak;
@@ -585,6 +592,7 @@ int rtc_set_gain(rtc_handle* h, float gain, float leak) {
 
 int rtc_reset(rtc_handle* h) {
     if (!h) return RTC_EINVAL;
+    if (h->in_slot.load()) return fail(h, RTC_ESTATE, "the handle's job is in a server slot");
     DeviceScope ds(h->cfg.device);
     RTC_CUDA(h, cudaMemsetAsync(h->d_a, 0, h->cfg.nact * sizeof(float), h->stream));
     if (h->d_ring)
@@ -596,6 +604,7 @@ int rtc_reset(rtc_handle* h) {
 
 int rtc_load_predictor(rtc_handle* h, const float* params, int64_t n, float sigma) {
     if (!h) return RTC_EINVAL;
+    if (h->in_slot.load()) return fail(h, RTC_ESTATE, "the handle's job is in a server slot");
     if (!params || n != RTC_MLP_NPARAMS || !(sigma > 0.f) || !isfinite(sigma))
         return fail(h, RTC_EINVAL, "need RTC_MLP_NPARAMS parameters and sigma > 0");
     if (h->cfg.n_wfs != 1) return fail(h, RTC_EINVAL, "the predictor is for single-WFS handles");
@@ -635,6 +644,7 @@ int rtc_load_predictor(rtc_handle* h, const float* params, int64_t n, float sigm
 
 int rtc_set_predictor(rtc_handle* h, int32_t on) {
     if (!h) return RTC_EINVAL;
+    if (h->in_slot.load()) return fail(h, RTC_ESTATE, "the handle's job is in a server slot");
     if (on && !h->pred) return fail(h, RTC_ESTATE, "no predictor loaded");
     h->pred_on = on != 0;
     return RTC_OK;
@@ -642,6 +652,7 @@ int rtc_set_predictor(rtc_handle* h, int32_t on) {
 
 int rtc_get_dm(rtc_handle* h, float* out) {
     if (!h || !out) return h ? fail(h, RTC_EINVAL, "out is NULL") : RTC_EINVAL;
+    if (h->in_slot.load()) return fail(h, RTC_ESTATE, "the handle's job is in a server slot");
     DeviceScope ds(h->cfg.device);
     RTC_CUDA(h, cudaMemcpyAsync(out, h->d_a, h->cfg.nact * sizeof(float), cudaMemcpyDeviceToHost, h->stream));
     RTC_CUDA(h, cudaStreamSynchronize(h->stream));
@@ -675,6 +686,7 @@ int rtc_get_info(const rtc_handle* h, rtc_info* out) {
 int rtc_process_frame(rtc_handle* h, const uint16_t* frame, float* dm_out, float* slopes_out) {
     int rc = check_ready(h);
     if (rc != RTC_OK) return rc;
+    if (h->in_slot.load()) return fail(h, RTC_ESTATE, "the handle's job is in a server slot");
     if (!frame || !dm_out) return fail(h, RTC_EINVAL, "frame and dm_out must be non-NULL");
     DeviceScope ds(h->cfg.device);
     const size_t fbytes = static_cast<size_t>(h->cfg.n_wfs) * h->side * h->side * sizeof(uint16_t);
@@ -713,6 +725,7 @@ int rtc_process_frame_async(rtc_handle* h, const uint16_t* d_frame, float* d_dm_
                             float* d_slopes_out, void* stream) {
     int rc = check_ready(h);
     if (rc != RTC_OK) return rc;
+    if (h->in_slot.load()) return fail(h, RTC_ESTATE, "the handle's job is in a server slot");
     if (!d_frame) return fail(h, RTC_EINVAL, "d_frame is NULL");
     if (reinterpret_cast<uintptr_t>(d_frame) & 15) return fail(h, RTC_EINVAL, "d_frame must be 16-byte aligned");
     DeviceScope ds(h->cfg.device);
@@ -722,6 +735,7 @@ int rtc_process_frame_async(rtc_handle* h, const uint16_t* d_frame, float* d_dm_
 
 int rtc_centroid_async(rtc_handle* h, const uint16_t* d_frame, float* d_slopes_out, void* stream) {
     if (!h) return RTC_EINVAL;
+    if (h->in_slot.load()) return fail(h, RTC_ESTATE, "the handle's job is in a server slot");
     if (!h->calib_loaded) return fail(h, RTC_ESTATE, "calibration maps not loaded");
     if (!d_frame) return fail(h, RTC_EINVAL, "d_frame is NULL");
     if (reinterpret_cast<uintptr_t>(d_frame) & 15) return fail(h, RTC_EINVAL, "d_frame must be 16-byte aligned");
@@ -736,6 +750,7 @@ int rtc_centroid_async(rtc_handle* h, const uint16_t* d_frame, float* d_slopes_o
 
 int rtc_reconstruct_async(rtc_handle* h, const float* d_slopes, float* d_dm_out, void* stream) {
     if (!h) return RTC_EINVAL;
+    if (h->in_slot.load()) return fail(h, RTC_ESTATE, "the handle's job is in a server slot");
     if (h->store < 0) return fail(h, RTC_ESTATE, "control matrix not loaded");
     DeviceScope ds(h->cfg.device);
     cudaStream_t st = stream ? static_cast<cudaStream_t>(stream) : h->stream;

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
 #include <functional>
 #include <string>
 #include <vector>
@@ -97,7 +98,7 @@ struct rtc_handle {
     rtc_loop_done* h_done = nullptr;          // pinned mapped [RTC_LOOP_SLOTS]
     int sbuf_kpad = -1;                       // kpad d_sbuf was sized for
 
-    bool in_slot = false;                     // owned by a server slot (rtc_slot_submit)
+    std::atomic<bool> in_slot{false};         // owned by a server slot (rtc_slot_submit)
 
     // learned slope predictor (rtc_load_predictor)
     struct MlpDev* pred = nullptr;            // network weights on the device

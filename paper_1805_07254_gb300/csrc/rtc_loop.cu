@@ -100,6 +100,7 @@ int ensure_buffers(rtc_handle* h) {
 
 extern "C" int rtc_run_loop(rtc_handle* h, const rtc_loop_config* cfg, rtc_stats* stats) {
     if (!h) return RTC_EINVAL;
+    if (h->in_slot.load()) return fail_handle(h, RTC_ESTATE, "the handle's job is in a server slot");
     if (!cfg || !stats) return fail_handle(h, RTC_EINVAL, "cfg and stats must be non-NULL");
     if (!h->calib_loaded || h->store < 0)
         return fail_handle(h, RTC_ESTATE, "calibration maps and control matrix must be loaded");

@@ -180,8 +180,12 @@ class Rtc:
             raise RtcError(rc, self._lib.rtc_last_error(self._h).decode())
 
     def close(self):
+        """Release the handle (rtc_destroy); raises RtcError (RTC_ESTATE) while its job is
+        in a server slot, keeping the handle."""
         if getattr(self, "_h", None):
-            self._lib.rtc_destroy(self._h)
+            rc = self._lib.rtc_destroy(self._h)
+            if rc == RTC_ESTATE:
+                raise RtcError(rc, self._lib.rtc_last_error(self._h).decode())
             self._h = None
 
     def __del__(self):

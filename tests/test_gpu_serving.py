@@ -93,3 +93,32 @@ def test_jobs_overlap_on_the_device():
     both = time.perf_counter() - t0
     print(f"two jobs back to back {serial * 1e3:.1f} ms, together {both * 1e3:.1f} ms")
     assert both < 0.9 * serial
+
+
+def test_handle_calls_are_refused_while_its_job_is_in_a_slot():
+    """The job's kernels use the handle's device state: until the job is done the
+    handle's own calls return RTC_ESTATE (rtc_destroy included), then it works again."""
+    from paper_1805_07254_gb300 import Server
+    from paper_1805_07254_gb300.rtc import RtcError, RTC_ESTATE
+    cfg = synth.elt_scao()
+    frames, _ = synth.make_frames(cfg, 0, 4)
+    frames = np.tile(frames.numpy(), (80, 1, 1, 1))          # 320 ELT frames, ~15 ms of work
+    r, oracle, M, *_ = make_pair(cfg)
+    srv = Server(max_slots=2)
+    slot = srv.submit(r, frames)
+    if srv.poll(slot)[0]:
+        pytest.skip("the job finished before the checks")
+    for call in (lambda: r.load_cmat(M), lambda: r.set_readout(74, 10.0), lambda: r.reset(),
+                 lambda: r.process_frame(frames[0]), lambda: r.close()):
+        with pytest.raises(RtcError) as e:
+            call()
+        assert e.value.code == RTC_ESTATE
+    assert not srv.poll(slot)[0], "the job must still have been running for the checks to count"
+    dm = srv.wait(slot)
+    assert dm.shape == (frames.shape[0], cfg.nact)
+    r.reset()
+    oracle.a[:] = 0
+    a_ref, _ = oracle.step(frames[0])
+    assert rel_rms(r.process_frame(frames[0]), a_ref) <= 1e-5
+    r.close()
+    srv.close()
