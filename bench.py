@@ -188,7 +188,9 @@ def oracle_worker(path):
     print(json.dumps({"times_us": times}))
 
 
-def run_oracle(cfg, frames, dark, flat, M, budget_s, max_frames):
+def run_oracle(cfg, frames, dark, flat, M, budget_s, max_frames, threads=1):
+    """Per-frame times (us) of the FP64 oracle in a child process whose BLAS and
+    OpenMP pools have `threads` threads."""
     import numpy as np
     fd, path = tempfile.mkstemp(suffix=".npz")
     os.close(fd)
@@ -196,7 +198,7 @@ def run_oracle(cfg, frames, dark, flat, M, budget_s, max_frames):
              leak=cfg.leak, frames=frames, budget_s=budget_s, max_frames=max_frames)
     env = dict(os.environ)
     for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "NUMEXPR_NUM_THREADS"):
-        env[v] = "1"
+        env[v] = str(threads)
     try:
         out = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-worker", path],
                              capture_output=True, text=True, env=env, timeout=budget_s + 300)
@@ -515,12 +517,19 @@ def ours(args):
     worst, total_fps = reduce_replicas(torch, dist if world > 1 else None, s_step, dev)
     value = worst["p50"]
 
-    cpu = None
+    cpu = cpu_all = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         times = run_oracle(cfg, frames[:4], dark, flat, M, args.cpu_sample_s, 400)
         cpu = {"value": round(pct(times, 0.5), 1), "unit": "us", "cores": 1, "kind": "oracle",
                "sample": f"{len(times)} ELT frames through the FP64 oracle (single thread, "
                          f"time-bounded at {args.cpu_sample_s:.0f} s); p50 per frame"}
+        # the same oracle with every host core in its BLAS pool (context for the single-thread
+        # baseline: the 281 MB FP64 matrix-vector product is host-memory-bound)
+        ncores = os.cpu_count() or 1
+        times_mt = run_oracle(cfg, frames[:4], dark, flat, M, args.cpu_sample_s / 2, 400, threads=ncores)
+        cpu_all = {"value": round(pct(times_mt, 0.5), 1), "unit": "us", "cores": ncores, "kind": "oracle",
+                   "sample": f"{len(times_mt)} ELT frames through the FP64 oracle with {ncores} BLAS "
+                             f"threads (time-bounded at {args.cpu_sample_s / 2:.0f} s); p50 per frame"}
 
     traffic = recorded_traffic(f"elt_{args.store}")
     floor_us = launch_floor(torch, flush, st, min(args.steps, 1000))
@@ -554,6 +563,7 @@ def ours(args):
         "stress_6wfs_fp8": stress,
         "loop": loop,
         "cpu_baseline": cpu,
+        "cpu_baseline_all_cores": cpu_all,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
