@@ -23,7 +23,8 @@ device kernels:
 Parity pins (tests/test_oracle_pins.py): GELU against scipy's erf (a library
 routine); the analytic backward against central finite differences of the
 forward; Adam's first step against its closed form (a step of lr * sign(g));
-the gather against brute-force placement of marked values on the grid.
+the gather against brute-force placement of marked values on the grid, and
+the table-driven gather against the loop gather on both geometries.
 """
 from __future__ import annotations
 
@@ -56,6 +57,41 @@ def gather_features(history, subaps, nsub, sigma=1.0):
                             j = grid_idx[rr, cc]
                             f = ((lag * 2 + axis) * 5 + (dr + HALF)) * 5 + (dc + HALF)
                             X[i, f] = history[lag, axis * nv + j] / sigma
+    return X
+
+
+def neighbour_table(subaps, nsub):
+    """(nv x 25) index of each subaperture's 5x5 neighbours, (dr, dc) row-major, -1 where
+    the neighbour is off the grid or off the pupil -- the same placement rule as
+    ``gather_features``, tabulated once so that long runs can gather by indexing."""
+    subaps = np.asarray(subaps)
+    nv = subaps.shape[0]
+    grid_idx = -np.ones((nsub, nsub), dtype=np.int64)
+    grid_idx[subaps[:, 0], subaps[:, 1]] = np.arange(nv)
+    table = -np.ones((nv, (2 * HALF + 1) ** 2), dtype=np.int64)
+    for dr in range(-HALF, HALF + 1):
+        for dc in range(-HALF, HALF + 1):
+            rr, cc = subaps[:, 0] + dr, subaps[:, 1] + dc
+            inside = (rr >= 0) & (rr < nsub) & (cc >= 0) & (cc < nsub)
+            nb = (dr + HALF) * (2 * HALF + 1) + (dc + HALF)
+            table[inside, nb] = grid_idx[rr[inside], cc[inside]]
+    return table
+
+
+def gather_features_table(history, table, sigma=1.0):
+    """``gather_features`` by indexing with a ``neighbour_table``: X (nv x 200) with
+    ``X[i, (lag*2 + axis)*25 + nb] = history[lag, axis*nv + table[i, nb]] / sigma``
+    (0 where the table holds -1)."""
+    history = np.asarray(history, dtype=np.float64)
+    nv = table.shape[0]
+    X = np.zeros((nv, NFEAT), dtype=np.float64)
+    ok = table >= 0
+    j = np.where(ok, table, 0)
+    for lag in range(LAGS):
+        for axis in range(2):
+            vals = history[lag, axis * nv + j] / sigma
+            f0 = (lag * 2 + axis) * 25
+            X[:, f0:f0 + 25] = np.where(ok, vals, 0.0)
     return X
 
 

@@ -46,7 +46,7 @@ struct rtc_server {
     int64_t in_use = 0;
     std::vector<Job> jobs;
     std::vector<cudaStream_t> streams;
-    std::mutex mu;
+    mutable std::mutex mu;
 };
 
 namespace {
@@ -212,6 +212,7 @@ int rtc_slot_poll(rtc_server* s, int32_t slot, uint64_t* frames_done) {
 
 int rtc_server_info(const rtc_server* s, int32_t* active_slots, int64_t* mem_in_use) {
     if (!s) return RTC_EINVAL;
+    std::lock_guard<std::mutex> lock(s->mu);    // submit and poll change both fields under it
     int n = 0;
     for (const Job& j : s->jobs) n += j.active ? 1 : 0;
     if (active_slots) *active_slots = n;

@@ -214,27 +214,6 @@ def test_reset_and_gain_changes():
     _run_and_compare(r, oracle, frames[1:].numpy())
 
 
-def test_stress_six_wfs_fp8_sampled_rows():
-    """Stress sizing: 6 WFS stacked into one 4421 x 47664 FP8 matrix.  The oracle
-    checks slopes fully and DM commands on a sample of rows."""
-    cfg = synth.elt_scao_6wfs()
-    frames, _ = synth.make_frames(cfg, 0, 1)
-    raw = frames[0].numpy()
-    from paper_1805_07254_gb300 import Rtc
-    dark, flat = synth.calibration_maps(cfg)
-    M = synth.control_matrix(cfg).numpy()
-    r = Rtc(cfg.nsub, cfg.npx, cfg.nact, n_wfs=cfg.n_wfs, obs=cfg.obs, gain=cfg.gain, leak=cfg.leak)
-    r.load_calib(dark.numpy(), flat.numpy())
-    r.load_cmat(M, store="fp8")
-    dm, s = r.process_frame(raw, want_slopes=True)
-    s_ref = P.slopes(raw, dark.numpy(), flat.numpy(), cfg.subaps, cfg.npx)
-    assert np.max(np.abs(s - s_ref)) <= SLOPE_TOL
-    rows = np.random.default_rng(0).choice(cfg.nact, 64, replace=False)
-    q, sc = Q.fp8_row_quantise(M[rows])
-    ref = cfg.gain * ((sc.astype(np.float64)[:, None] * q) @ s_ref)
-    assert rel_rms(dm[rows], ref) <= DM_TOL
-
-
 @pytest.mark.parametrize("store", ["f32", "bf16", "f16", "fp8", "int8"])
 def test_fused_frame_kernel_equals_stage_kernels(store):
     """rtc_process_frame_async (one fused cooperative kernel) and the two stage calls

@@ -413,3 +413,18 @@ def test_gather_places_each_neighbour():
             j = pos.get((r + dr, c + dc))
             want = 0.0 if j is None else 1 + 10000 * lag + 1000 * axis + j
             assert X[i, f] == want
+
+
+@pytest.mark.parametrize("name", ["tiny", "elt"])
+def test_table_gather_equals_loop_gather(name):
+    """The indexed gather used for long runs places every value where the loop gather
+    does (the loop gather is itself pinned above by brute-force placement)."""
+    cfg = synth.CONFIGS[name]()
+    sa = cfg.subaps
+    nv = sa.shape[0]
+    hist = np.random.default_rng(3).standard_normal((4, 2 * nv))
+    table = L.neighbour_table(sa, cfg.nsub)
+    assert table.shape == (nv, 25)
+    assert np.all(table[:, 12] == np.arange(nv))          # the centre is the subaperture itself
+    np.testing.assert_array_equal(L.gather_features_table(hist, table, 0.3),
+                                  L.gather_features(hist, sa, cfg.nsub, 0.3))

@@ -71,6 +71,63 @@ def test_noalloc_matches_handle_path_on_two_calls(store):
     r.close()
 
 
+def _stored_codes(M, store, kpad):
+    """The caller's buffers for a stored type: [nact][kpad] codes (zero padded) and row
+    scales (FP8 and INT8), from the oracle's quantisers."""
+    from oracle import quant as Q
+    nact, ns = M.shape
+    scales = None
+    if store == "f32":
+        codes = torch.zeros((nact, kpad), dtype=torch.float32)
+        codes[:, :ns] = torch.from_numpy(M)
+    elif store == "fp8":
+        q, scales = Q.fp8_row_quantise(M)
+        codes = torch.zeros((nact, kpad), dtype=torch.float8_e4m3fn)
+        codes[:, :ns] = torch.from_numpy(q).float().to(torch.float8_e4m3fn)
+    else:
+        q, scales = Q.int8_row_quantise(M)
+        codes = torch.zeros((nact, kpad), dtype=torch.int8)
+        codes[:, :ns] = torch.from_numpy(q.astype(np.int8))
+    return codes, scales
+
+
+@pytest.mark.parametrize("store", ["f32", "fp8", "int8"])
+@pytest.mark.parametrize("ksplit", [1, 16])
+def test_noalloc_matches_oracle_on_two_calls(store, ksplit):
+    """Every stored type with its row scales, no split (no partials written) and the
+    largest split the scratch holds, an odd actuator count (69): DM commands of two
+    calls in a row against the FP64 oracle on the stored matrix."""
+    from oracle import pipeline as P
+    from oracle import quant as Q
+    from paper_1805_07254_gb300.rtc import mvm_integrate_noalloc
+
+    cfg = synth.tiny_scao()
+    nact, ns = cfg.nact, cfg.nslopes
+    kpad = (ns + 15) // 16 * 16
+    M = synth.control_matrix(cfg).numpy()
+    dev = torch.device("cuda:0")
+    codes, scales = _stored_codes(M, store, kpad)
+    d_M = codes.to(dev)
+    d_sc = torch.from_numpy(scales).to(dev) if scales is not None else None
+    Ms = Q.stored_matrix(M, store)
+    rng = np.random.default_rng(1)
+    d_s = torch.zeros(kpad, dtype=torch.float32, device=dev)
+    d_a = torch.zeros(nact, dtype=torch.float32, device=dev)
+    d_dm = torch.full((nact,), np.nan, dtype=torch.float32, device=dev)
+    a_ref = np.zeros(nact)
+    st = torch.cuda.current_stream()
+    for _ in range(2):
+        s = (0.3 * rng.standard_normal(ns)).astype(np.float32)
+        d_s[:ns] = torch.from_numpy(s).to(dev)
+        mvm_integrate_noalloc(d_M, store, d_sc, nact, kpad, d_s, d_a, d_dm, cfg.gain, cfg.leak,
+                              ksplit, stream=st)
+        torch.cuda.synchronize()
+        a_ref = P.integrate(a_ref, P.reconstruct(Ms, s), cfg.gain, cfg.leak)
+        got = d_dm.cpu().numpy()
+        assert rel_rms(got, a_ref) <= DM_TOL, rel_rms(got, a_ref)
+        np.testing.assert_array_equal(d_a.cpu().numpy(), got)
+
+
 def test_noalloc_rejects_sizes_beyond_its_scratch():
     from paper_1805_07254_gb300.rtc import RtcError, RTC_EINVAL, mvm_integrate_noalloc
     dev = torch.device("cuda:0")
