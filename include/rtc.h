@@ -285,6 +285,11 @@ typedef struct rtc_loop_config {
                                     the rows its subapertures cover have arrived (the
                                     paper's processing of pixels during readout, Sec. 2.2). */
     double band_interval_us;     /* host time between the publication of successive bands */
+    int32_t matrix_l2;           /* 0: a matrix of at most 80 MB is streamed with the default
+                                    L2 policy, so that it can stay in L2 from frame to frame,
+                                    a larger one with L2 evict_first; 1: evict_first whatever
+                                    its size (lines may still hit L2 when nothing else
+                                    competes for it) */
 } rtc_loop_config;
 
 /* Latency statistics of one rtc_run_loop call.  "e2e": host clock, from the flag

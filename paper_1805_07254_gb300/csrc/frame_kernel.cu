@@ -19,7 +19,16 @@
 // With the learned slope predictor on (PRED), the measured slopes go into the
 // history ring, a grid barrier makes them visible, each block predicts the next
 // slopes of its own subapertures from their neighbourhoods (pred_tile.cuh, in the
-// shared scratch before the slopes) and multiplies the prediction.
+// shared scratch before the slopes), writing them straight into its local slope
+// vector, and multiplies the prediction.  The producer's hold then lasts through the
+// barrier and the prediction, so it prefetches further tiles into L2 before it
+// waits and the HBM keeps streaming.
+//
+// For rtc_process_frame with pinned host buffers (HOST) the frame is read in place
+// from mapped host memory and the DM commands are written there; the last block to
+// finish writes the caller's completion record, so the host needs no copies and no
+// stream synchronisation.  This is a separate instantiation: the device-frame kernel
+// carries none of its code.
 //
 // The grid barrier counts block arrivals on a 64-bit counter that only grows;
 // each barrier waits for the running total of arrivals expected up to and
@@ -32,6 +41,29 @@
 #include "pred_tile.cuh"
 #include "stream_mvm.cuh"
 
+#ifndef RTC_PRED_L2_TILES
+#define RTC_PRED_L2_TILES 4
+#endif
+
+#ifdef RTC_PHASE_STAMPS
+// Diagnostic build only: %globaltimer at the phases of each block of the last launch.
+__device__ unsigned long long g_rtc_stamps[256][8];
+#define RTC_STAMP(i)                                                   \
+    do {                                                               \
+        if (tid == 0) g_rtc_stamps[blockIdx.x][i] = rtc_mvm::global_ns(); \
+    } while (0)
+extern "C" int rtc_probe_stamps(unsigned long long* out, int n) {
+    return cudaMemcpyFromSymbol(out, g_rtc_stamps, sizeof(unsigned long long) * 8 * (n < 256 ? n : 256)) ==
+                   cudaSuccess
+               ? 0
+               : -1;
+}
+#else
+#define RTC_STAMP(i) \
+    do {             \
+    } while (0)
+#endif
+
 namespace {
 
 using namespace rtc_mvm;
@@ -41,20 +73,27 @@ using namespace rtc_mvm;
 constexpr int kGateBar = 4;
 // Matrix tiles the producer streams before the block's slopes are known.
 constexpr int kPrefetchTiles = 1;
+// With the predictor the hold lasts through the grid barrier and the prediction:
+// this many further tiles stream into L2 meanwhile.
+constexpr int kPredL2Tiles = RTC_PRED_L2_TILES;
 
-template <int DT, int NPX, bool PRED>
+// HOST: the frame is in mapped host memory (rtc_process_frame with pinned buffers):
+// it is read with uncached loads over the host link, and the last block to finish
+// writes the caller's completion record (fh).
+template <int DT, int NPX, bool PRED, bool HOST>
 __global__ void __launch_bounds__(kThreads, 1)
 frame_kernel(rtc_pixel::PixelArgs px, Args g, rtc_pred::PredArgs pa, int head,
-             unsigned long long* gridbar, unsigned long long target) {
+             unsigned long long* gridbar, unsigned long long target, FrameHost fh) {
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ Shared sh;
     const int tid = threadIdx.x;
+    RTC_STAMP(0);
     if (tid == 0) init_shared(sh);
     __syncthreads();
     const Plan pl = make_plan(g, smem);
     if (tid >= kConsumers) {
         asm volatile("bar.sync %0, %1;" ::"n"(kGateBar), "n"(kThreads) : "memory");
-        if ((tid & 31) == 0) produce(g, pl, sh, 0, true, kPrefetchTiles);
+        if ((tid & 31) == 0) produce(g, pl, sh, 0, true, kPrefetchTiles, PRED ? kPredL2Tiles : 0);
         return;
     }
     clear_local(g, pl, tid);
@@ -62,6 +101,7 @@ frame_kernel(rtc_pixel::PixelArgs px, Args g, rtc_pred::PredArgs pa, int head,
 
     // pixel stage: the block's subapertures, one half-warp each (the ~26
     // subapertures of a block on the ELT frame take a single round)
+    constexpr int kLoad = HOST ? rtc_pixel::kPixelVolatile : rtc_pixel::kPixelReadOnly;
     const int slot = 2 * (tid >> 5) + ((tid >> 4) & 1);
     bool gate_open = false;             // every consumer warp arrives exactly once
     auto open_gate = [&gate_open]() {
@@ -73,8 +113,8 @@ frame_kernel(rtc_pixel::PixelArgs px, Args g, rtc_pred::PredArgs pa, int head,
     for (int base = pl.g0; base < pl.g1; base += 2 * kConsumerWarps) {
         const int gi = base + slot;
         const bool valid = gi < pl.g1;
-        const float2 sxy = rtc_pixel::subap_slopes<NPX, rtc_pixel::kPixelReadOnly, 16>(
-            px, px.frame, px.s, gi, valid, tid & 31, open_gate);
+        const float2 sxy =
+            rtc_pixel::subap_slopes<NPX, kLoad, 16>(px, px.frame, px.s, gi, valid, tid & 31, open_gate);
         if (valid && (tid & 15) == 0) {
             int ix, iy;
             local_index(g, pl, gi, ix, iy);
@@ -83,6 +123,7 @@ frame_kernel(rtc_pixel::PixelArgs px, Args g, rtc_pred::PredArgs pa, int head,
         }
     }
     open_gate();                        // a warp without pixel work
+    RTC_STAMP(1);
     prefetch_rows<DT>(g, pl, tid);
 
     unsigned long long next = target;   // arrivals that complete the next grid barrier
@@ -97,39 +138,72 @@ frame_kernel(rtc_pixel::PixelArgs px, Args g, rtc_pred::PredArgs pa, int head,
         consumer_sync();
         next += gridDim.x;
         if (!sh.abort_flag) {
-            rtc_pred::predict(pa, pl.scratch, tid, pl.g0, pl.g1, head, pr);
-            gather_local(g, pl, tid, pa.s_pred, true);
+            // the predictions replace the block's local slopes as they are made
+            rtc_pred::predict(pa, pl.scratch, tid, pl.g0, pl.g1, head, pr, [&](int gi, int axis, float v) {
+                int ix, iy;
+                local_index(g, pl, gi, ix, iy);
+                pl.loc[axis ? iy : ix] = v;
+            });
         }
     }
     consumer_sync();
+    RTC_STAMP(2);
     if (tid == 0) sh.release = 1;       // the rest of the matrix stream may start
     consume<DT>(g, pl, sh, tid, 0);
+    RTC_STAMP(3);
 
     // every block's partial vectors before any block sums them
     consumer_sync();
     if (tid == 0 && !sh.abort_flag) grid_barrier(gridbar, next, g.status, &sh.abort_flag);
     consumer_sync();
+    RTC_STAMP(4);
     if (!sh.abort_flag) reduce_rows<DT>(g, pl, tid, g.dm_out);
+    RTC_STAMP(5);
+
+    if (HOST) {
+        // the last block to finish writes the completion record (every block, aborted
+        // or not, counts itself once)
+        consumer_sync();
+        if (tid == 0) {
+            __threadfence_system();
+            const unsigned long long prev = atomicAdd(fh.ctr, 1ull);
+            if (prev + 1 == fh.target) {
+                __threadfence_system();
+                fh.done->status = *reinterpret_cast<volatile int*>(g.status);
+                __threadfence_system();
+                asm volatile("st.release.sys.global.u64 [%0], %1;" ::"l"(&fh.done->seq), "l"(fh.seq) : "memory");
+            }
+        }
+    }
 }
 
-template <int DT, int NPX, bool PRED>
+template <int DT, int NPX, bool PRED, bool HOST>
 cudaError_t launch_t(const Launch& L, rtc_pixel::PixelArgs px, Args g, rtc_pred::PredArgs pa, int head,
-                     unsigned long long* bar, unsigned long long target, cudaStream_t st) {
-    void* args[] = {&px, &g, &pa, &head, &bar, &target};
-    return cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(frame_kernel<DT, NPX, PRED>),
+                     unsigned long long* bar, unsigned long long target, FrameHost fh, cudaStream_t st) {
+    void* args[] = {&px, &g, &pa, &head, &bar, &target, &fh};
+    return cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(frame_kernel<DT, NPX, PRED, HOST>),
                                        dim3(L.G), dim3(kThreads), args, L.smem, st);
 }
 
-template <int DT, bool PRED>
+template <int DT, bool PRED, bool HOST>
 cudaError_t launch_npx(const rtc_handle* h, const Launch& L, rtc_pixel::PixelArgs px, Args g,
-                       rtc_pred::PredArgs pa, int head, unsigned long long target, cudaStream_t st) {
-    if (h->cfg.npx == 10) return launch_t<DT, 10, PRED>(L, px, g, pa, head, h->d_gridbar, target, st);
-    return launch_t<DT, 0, PRED>(L, px, g, pa, head, h->d_gridbar, target, st);
+                       rtc_pred::PredArgs pa, int head, unsigned long long target, const FrameHost& fh,
+                       cudaStream_t st) {
+    if (h->cfg.npx == 10) return launch_t<DT, 10, PRED, HOST>(L, px, g, pa, head, h->d_gridbar, target, fh, st);
+    return launch_t<DT, 0, PRED, HOST>(L, px, g, pa, head, h->d_gridbar, target, fh, st);
+}
+
+template <int DT, bool HOST>
+cudaError_t launch_pred(const rtc_handle* h, const Launch& L, rtc_pixel::PixelArgs px, Args g, bool pred,
+                        int head, unsigned long long target, const FrameHost& fh, cudaStream_t st) {
+    if (pred) return launch_npx<DT, true, HOST>(h, L, px, g, pred_args(h), head, target, fh, st);
+    const rtc_pred::PredArgs pa{};
+    return launch_npx<DT, false, HOST>(h, L, px, g, pa, 0, target, fh, st);
 }
 
 template <int DT>
 cudaError_t launch_dt(rtc_handle* h, const uint16_t* d_frame, float* d_dm_out, float* d_s_meas,
-                      int head, cudaStream_t st) {
+                      int head, cudaStream_t st, FrameHost* fhp) {
     const bool pred = d_s_meas != nullptr;
     const Launch L = plan_launch(h, pred ? rtc_pred::kSmemBytes : 0);
     if (!L.ok) return cudaErrorInvalidValue;
@@ -139,29 +213,39 @@ cudaError_t launch_dt(rtc_handle* h, const uint16_t* d_frame, float* d_dm_out, f
     // each target is the running total of expected arrivals, not launches x blocks
     const unsigned long long G = static_cast<unsigned long long>(L.G);
     const unsigned long long target = h->grid_epoch + G;
-    cudaError_t e;
-    if (pred) {
-        e = launch_npx<DT, true>(h, L, px, g, pred_args(h), head, target, st);
-    } else {
-        const rtc_pred::PredArgs pa{};
-        e = launch_npx<DT, false>(h, L, px, g, pa, 0, target, st);
+    FrameHost fh{};
+    if (fhp) {
+        fh = *fhp;
+        fh.target = h->pf_arrivals + G;
     }
-    if (e == cudaSuccess) h->grid_epoch = target + (pred ? G : 0);
+    const cudaError_t e = fhp ? launch_pred<DT, true>(h, L, px, g, pred, head, target, fh, st)
+                              : launch_pred<DT, false>(h, L, px, g, pred, head, target, fh, st);
+    if (e == cudaSuccess) {
+        h->grid_epoch = target + (pred ? G : 0);
+        if (fhp) h->pf_arrivals = fh.target;
+    }
     return e;
 }
 
-template <int DT, int NPX, bool PRED>
+template <int DT, int NPX, bool PRED, bool HOST>
 cudaError_t configure_t() {
-    return cudaFuncSetAttribute(frame_kernel<DT, NPX, PRED>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    return cudaFuncSetAttribute(frame_kernel<DT, NPX, PRED, HOST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 static_cast<int>(kDynSmemBudget));
+}
+
+template <int DT, bool HOST>
+cudaError_t configure_host() {
+    cudaError_t e = configure_t<DT, 10, false, HOST>();
+    if (e == cudaSuccess) e = configure_t<DT, 0, false, HOST>();
+    if (e == cudaSuccess) e = configure_t<DT, 10, true, HOST>();
+    if (e == cudaSuccess) e = configure_t<DT, 0, true, HOST>();
+    return e;
 }
 
 template <int DT>
 cudaError_t configure_dt() {
-    cudaError_t e = configure_t<DT, 10, false>();
-    if (e == cudaSuccess) e = configure_t<DT, 0, false>();
-    if (e == cudaSuccess) e = configure_t<DT, 10, true>();
-    if (e == cudaSuccess) e = configure_t<DT, 0, true>();
+    cudaError_t e = configure_host<DT, false>();
+    if (e == cudaSuccess) e = configure_host<DT, true>();
     return e;
 }
 
@@ -192,14 +276,14 @@ rtc_pred::PredArgs pred_args(const rtc_handle* h) {
 }
 
 cudaError_t launch_frame(rtc_handle* h, const uint16_t* d_frame, float* d_dm_out, float* d_s_meas,
-                         int head, cudaStream_t st) {
+                         int head, cudaStream_t st, FrameHost* fh) {
     if (h->kpad == 0) return launch_decay(h, d_dm_out, st);
     switch (h->store) {
-        case RTC_F32: return launch_dt<RTC_F32>(h, d_frame, d_dm_out, d_s_meas, head, st);
-        case RTC_BF16: return launch_dt<RTC_BF16>(h, d_frame, d_dm_out, d_s_meas, head, st);
-        case RTC_F16: return launch_dt<RTC_F16>(h, d_frame, d_dm_out, d_s_meas, head, st);
-        case RTC_FP8_E4M3: return launch_dt<RTC_FP8_E4M3>(h, d_frame, d_dm_out, d_s_meas, head, st);
-        case RTC_INT8: return launch_dt<RTC_INT8>(h, d_frame, d_dm_out, d_s_meas, head, st);
+        case RTC_F32: return launch_dt<RTC_F32>(h, d_frame, d_dm_out, d_s_meas, head, st, fh);
+        case RTC_BF16: return launch_dt<RTC_BF16>(h, d_frame, d_dm_out, d_s_meas, head, st, fh);
+        case RTC_F16: return launch_dt<RTC_F16>(h, d_frame, d_dm_out, d_s_meas, head, st, fh);
+        case RTC_FP8_E4M3: return launch_dt<RTC_FP8_E4M3>(h, d_frame, d_dm_out, d_s_meas, head, st, fh);
+        case RTC_INT8: return launch_dt<RTC_INT8>(h, d_frame, d_dm_out, d_s_meas, head, st, fh);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -23,7 +23,8 @@
 //   4. each block multiplies its matrix slices by its own slopes, a grid barrier
 //      publishes the partial DM vectors, and each block sums and integrates its
 //      share of the rows (stream_mvm.cuh); DM commands go to the device state and
-//      to the frame's slot in mapped host memory;
+//      to the frame's slot in mapped host memory.  The partial vectors alternate
+//      between two buffers frame by frame (see below);
 //   5. the last block to finish publishes the completion record (sequence, the
 //      latest device time at which a block had its rows, device time the commands
 //      were written).
@@ -34,7 +35,10 @@
 // Two blocks may both copy a unit that straddles their subapertures; they write
 // the same bytes of the same frame.  A block only starts copying frame k + 1 after
 // the grid barrier of frame k, which every block reaches after its pixel stage, so
-// no copy overwrites pixels another block is still reading.
+// no copy overwrites pixels another block is still reading.  In the same way a
+// block writes frame k + 2's partials (the buffer of frame k) only after the grid
+// barrier of frame k + 1, which every block reaches after summing its rows of
+// frame k (the barrier's release orders a block's earlier reads too).
 
 #include <algorithm>
 #include <vector>
@@ -65,6 +69,7 @@ struct LoopArgs {
     rtc_loop_done* done;               // mapped host [nslot]
     float* s_buf;                      // device [2][kpad]
     unsigned long long* gridbar;       // device, zero at launch
+    size_t partial_stride;             // floats between the two partial-vector buffers
     unsigned long long* donectr;       // device, zero at launch
     unsigned long long* t_seen;        // device [2], zero at launch
     unsigned long long n_frames;
@@ -238,19 +243,25 @@ __global__ void __launch_bounds__(kThreads, 1) loop_kernel(LoopArgs L) {
             if (tid == 0) grid_barrier(L.gridbar, G * (kBarriers * k + 1), L.mv.status, &sh.abort_flag);
             consumer_sync();
             if (sh.abort_flag) break;
-            rtc_pred::predict(L.pa, pl.scratch, tid, pl.g0, pl.g1, head, pr);
-            gather_local(L.mv, pl, tid, L.pa.s_pred, true);
+            // the predictions replace the block's local slopes as they are made
+            rtc_pred::predict(L.pa, pl.scratch, tid, pl.g0, pl.g1, head, pr, [&](int gi, int axis, float v) {
+                int ix, iy;
+                local_index(L.mv, pl, gi, ix, iy);
+                pl.loc[axis ? iy : ix] = v;
+            });
         }
         consumer_sync();
 
-        // 4. the block's partial DM vectors, then its rows summed and integrated;
-        //    DM commands to the device state and the frame's host slot
-        tile = consume<DT>(L.mv, pl, sh, tid, tile);
+        // 4. the block's partial DM vectors (this frame's buffer), then its rows summed
+        //    and integrated; DM commands to the device state and the frame's host slot
+        Args mv = L.mv;
+        mv.partial = L.mv.partial + (k & 1) * L.partial_stride;
+        tile = consume<DT>(mv, pl, sh, tid, tile);
         consumer_sync();
         if (tid == 0) grid_barrier(L.gridbar, G * (kBarriers * k + kBarriers), L.mv.status, &sh.abort_flag);
         consumer_sync();
         if (sh.abort_flag) break;
-        reduce_rows<DT>(L.mv, pl, tid, L.dm_ring + static_cast<size_t>(slot) * L.mv.nact);
+        reduce_rows<DT>(mv, pl, tid, L.dm_ring + static_cast<size_t>(slot) * L.mv.nact);
 
         // 5. the last block to finish publishes the completion record
         consumer_sync();
@@ -313,6 +324,7 @@ cudaError_t launch_dt(rtc_handle* h, const LoopLaunch& ll, cudaStream_t st) {
     LoopArgs a{};
     a.px = pixel_args(h, nullptr, nullptr);
     a.mv = make_args(h, nullptr, nullptr, Lc);
+    if (ll.l2_stream) a.mv.l2_policy = kL2Stream;
     a.frames = ll.d_frames;
     a.frame_elems = ll.frame_elems;
     a.stage = h->d_frame;
@@ -330,6 +342,7 @@ cudaError_t launch_dt(rtc_handle* h, const LoopLaunch& ll, cudaStream_t st) {
     a.done = ll.d_done;
     a.s_buf = h->d_sbuf;
     a.gridbar = h->d_gridbar;
+    a.partial_stride = static_cast<size_t>(h->dev_sms) * h->cfg.nact;
     a.donectr = h->d_donectr;
     a.t_seen = h->d_tseen;
     a.n_frames = ll.n_frames;

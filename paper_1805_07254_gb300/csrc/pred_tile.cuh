@@ -128,13 +128,19 @@ __device__ __forceinline__ void prefetch(const PredArgs& pa, int tid, int i0, in
     for (int q = 0; q < kPairRounds; ++q) r.jn[q] = pair_nbr(pa, i0, i1, tid + q * kConsumers);
 }
 
+struct NoSink {
+    __device__ void operator()(int, int, float) const {}
+};
+
 // After the grid barrier that completes the measured slopes: predictions of
 // subapertures [i0, i1) from the ring rows head, head-1, head-2, head-3 (newest
 // first), with the registers `prefetch` filled (before the barrier, so that the
 // weight and neighbour loads overlap the wait).  Every consumer thread calls it;
-// sm is TS-sample scratch of kSmemBytes.  Ends with a consumer barrier.
+// sm is TS-sample scratch of kSmemBytes.  Each prediction goes to pa.s_pred and to
+// sink(i, axis, value).  Ends with a consumer barrier.
+template <typename Sink = NoSink>
 __device__ __forceinline__ void predict(const PredArgs& pa, unsigned char* sm, int tid, int i0, int i1,
-                                        int head, const Regs& r) {
+                                        int head, const Regs& r, const Sink& sink = Sink()) {
     const int warp = tid >> 5, lane = tid & 31;
     const int g = lane >> 2, t = lane & 3;
     __nv_bfloat16* X = reinterpret_cast<__nv_bfloat16*>(sm + SM_X);
@@ -230,7 +236,9 @@ __device__ __forceinline__ void predict(const PredArgs& pa, unsigned char* sm, i
 #pragma unroll 16
                 for (int j = 0; j < NH; ++j) y = fmaf(H2[s * H2P + j], __ldg(W3 + o * NH + j), y);
                 const int idx = o * pa.nv + i;
-                pa.s_pred[idx] = __fmaf_rn(pa.sigma, y, __ldcg(rows[0] + idx));
+                const float sp = __fmaf_rn(pa.sigma, y, __ldcg(rows[0] + idx));
+                pa.s_pred[idx] = sp;
+                sink(i, o, sp);
             }
         }
         consumer_sync();

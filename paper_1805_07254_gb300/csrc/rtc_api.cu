@@ -8,6 +8,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <chrono>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -251,14 +252,14 @@ int check_ready(rtc_handle* h) {
 
 // s_used (optional) receives the device buffer that holds this frame's measured slopes.
 int enqueue_step(rtc_handle* h, const uint16_t* d_frame, float* d_dm_out, float* d_slopes_out,
-                 cudaStream_t st, const float** s_used = nullptr) {
+                 cudaStream_t st, const float** s_used = nullptr, FrameHost* fh = nullptr) {
     if (s_used) *s_used = h->d_s;
     if (h->pred_on && h->kpad > 0) {
         // measured slopes into the next row of the history ring, the prediction from
         // the 4 newest rows, the reconstruction from the prediction: one launch
         const int head = (h->ring_head + 1) & 3;
         float* s_meas = h->d_ring + static_cast<size_t>(head) * h->kpad;
-        RTC_CUDA(h, launch_frame(h, d_frame, d_dm_out, s_meas, head, st));
+        RTC_CUDA(h, launch_frame(h, d_frame, d_dm_out, s_meas, head, st, fh));
         h->ring_head = head;
         if (s_used) *s_used = s_meas;
         if (d_slopes_out)
@@ -266,10 +267,58 @@ int enqueue_step(rtc_handle* h, const uint16_t* d_frame, float* d_dm_out, float*
                                         cudaMemcpyDeviceToDevice, st));
         return RTC_OK;
     }
-    RTC_CUDA(h, launch_frame(h, d_frame, d_dm_out, nullptr, 0, st));
+    RTC_CUDA(h, launch_frame(h, d_frame, d_dm_out, nullptr, 0, st, fh));
     if (d_slopes_out)
         RTC_CUDA(h, cudaMemcpyAsync(d_slopes_out, h->d_s, h->nslopes * sizeof(float),
                                     cudaMemcpyDeviceToDevice, st));
+    return RTC_OK;
+}
+
+// Device view of a pinned, mapped host buffer; nullptr for pageable or device memory.
+const void* mapped_view(const void* p) {
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();             // clear the error of a pointer CUDA does not know
+        return nullptr;
+    }
+    return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+void* mapped_view(void* p) { return const_cast<void*>(mapped_view(static_cast<const void*>(p))); }
+
+constexpr double kHostWaitS = 2.0;      // bound on the host's wait for a frame's record
+
+// rtc_process_frame on pinned host buffers: one launch reads the frame over the host
+// link and writes the DM commands there; the host waits for the completion record.
+int process_mapped(rtc_handle* h, const uint16_t* d_frame_host, float* d_dm_host, float* slopes_out) {
+    if (!h->h_pf_done) {
+        void* p = nullptr;
+        RTC_CUDA(h, cudaHostAlloc(&p, sizeof(rtc_pf_done), cudaHostAllocMapped));
+        h->h_pf_done = static_cast<rtc_pf_done*>(p);
+        memset(h->h_pf_done, 0, sizeof(rtc_pf_done));
+        RTC_CUDA(h, cudaHostGetDevicePointer(reinterpret_cast<void**>(&h->d_pf_done), h->h_pf_done, 0));
+        RTC_CUDA(h, cudaMalloc(&h->d_pf_ctr, sizeof(unsigned long long)));
+        RTC_CUDA(h, cudaMemset(h->d_pf_ctr, 0, sizeof(unsigned long long)));
+        h->pf_arrivals = 0;
+    }
+    FrameHost fh{h->d_pf_done, h->d_pf_ctr, 0, ++h->pf_seq};
+    const float* s_used = nullptr;
+    const int rc = enqueue_step(h, d_frame_host, d_dm_host, nullptr, h->stream, &s_used, &fh);
+    if (rc != RTC_OK) return rc;
+    const auto t0 = std::chrono::steady_clock::now();
+    while (__atomic_load_n(&h->h_pf_done->seq, __ATOMIC_ACQUIRE) != fh.seq) {
+        if (std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count() > kHostWaitS) {
+            const cudaError_t e = cudaStreamSynchronize(h->stream);
+            if (e != cudaSuccess) return fail(h, RTC_EDEVICE, "%s", cudaGetErrorString(e));
+            if (__atomic_load_n(&h->h_pf_done->seq, __ATOMIC_ACQUIRE) == fh.seq) break;
+            return fail(h, RTC_ETIMEDOUT, "the frame's completion record did not arrive");
+        }
+    }
+    if (__atomic_load_n(&h->h_pf_done->status, __ATOMIC_RELAXED) != RTC_OK) return take_status(h, h->stream);
+    if (slopes_out) {
+        RTC_CUDA(h, cudaMemcpyAsync(slopes_out, s_used, h->nslopes * sizeof(float), cudaMemcpyDeviceToHost,
+                                    h->stream));
+        RTC_CUDA(h, cudaStreamSynchronize(h->stream));
+    }
     return RTC_OK;
 }
 
@@ -350,7 +399,7 @@ int rtc_create(const rtc_config* cfg, rtc_handle** out) {
     } else {
         const size_t frame_elems = static_cast<size_t>(c.n_wfs) * h->side * h->side;
         if (cudaMalloc(&h->d_a, c.nact * sizeof(float)) != cudaSuccess ||
-            cudaMalloc(&h->d_partial, static_cast<size_t>(h->dev_sms) * c.nact * sizeof(float)) != cudaSuccess ||
+            cudaMalloc(&h->d_partial, 2 * static_cast<size_t>(h->dev_sms) * c.nact * sizeof(float)) != cudaSuccess ||
             cudaMalloc(&h->d_frame, frame_elems * sizeof(uint16_t)) != cudaSuccess ||
             cudaMalloc(&h->d_status, sizeof(int)) != cudaSuccess ||
             cudaMalloc(&h->d_gridbar, sizeof(unsigned long long)) != cudaSuccess ||
@@ -397,6 +446,8 @@ int rtc_destroy(rtc_handle* h) {
     free_dev(h->d_tseen);
     free_dev(h->d_units);
     free_dev(h->d_blk);
+    free_dev(h->d_pf_ctr);
+    if (h->h_pf_done) cudaFreeHost(h->h_pf_done);
     if (h->h_ring) cudaFreeHost(h->h_ring);
     if (h->h_seq) cudaFreeHost(h->h_seq);
     if (h->h_dm_ring) cudaFreeHost(h->h_dm_ring);
@@ -689,6 +740,11 @@ int rtc_process_frame(rtc_handle* h, const uint16_t* frame, float* dm_out, float
     if (h->in_slot.load()) return fail(h, RTC_ESTATE, "the handle's job is in a server slot");
     if (!frame || !dm_out) return fail(h, RTC_EINVAL, "frame and dm_out must be non-NULL");
     DeviceScope ds(h->cfg.device);
+    // pinned (page-locked, mapped) host buffers: the kernel reads the frame and writes
+    // the commands over the host link, no copies and no stream synchronisation
+    const uint16_t* d_frame_host = static_cast<const uint16_t*>(mapped_view(frame));
+    float* d_dm_host = static_cast<float*>(mapped_view(dm_out));
+    if (d_frame_host && d_dm_host && h->kpad > 0) return process_mapped(h, d_frame_host, d_dm_host, slopes_out);
     const size_t fbytes = static_cast<size_t>(h->cfg.n_wfs) * h->side * h->side * sizeof(uint16_t);
     RTC_CUDA(h, cudaMemcpyAsync(h->d_frame, frame, fbytes, cudaMemcpyHostToDevice, h->stream));
     const float* s_used = nullptr;
@@ -714,7 +770,7 @@ int64_t rtc_handle_device_bytes(const rtc_handle* h) {
     int64_t b = h->m_bytes + 4 * nact;                                         // matrix + scales
     b += 2 * 4 * nw * h->n_valid * npp;                                        // dark + gain
     b += nw * static_cast<int64_t>(h->side) * h->side * 2;                     // frame staging
-    b += 4 * (kpad + nact) + 4 * static_cast<int64_t>(h->dev_sms) * nact + 4 * nact;  // s, a, partials
+    b += 4 * (kpad + nact) + 8 * static_cast<int64_t>(h->dev_sms) * nact + 4 * nact;  // s, a, partials
     if (h->pred) b += 4 * (5 * kpad) + 4 * 25 * h->n_valid + 3 * 4 * RTC_MLP_NPARAMS + 2 * (64 * 208 + 64 * 64);
     return b;
 }

@@ -27,6 +27,24 @@ struct rtc_loop_done {
     unsigned long long pad;
 };
 
+// Completion record of one rtc_process_frame call whose buffers are in pinned host
+// memory, written by the last block of the frame kernel into mapped host memory.
+struct rtc_pf_done {
+    unsigned long long seq;      // the call's sequence number once its DM commands are written
+    int status;                  // the device status word at that time (RTC_OK or an error)
+    int pad;
+};
+
+// What the frame kernel does for a caller waiting on the host (rtc_process_frame with
+// pinned buffers): the frame is read from mapped host memory, and the last block to
+// finish writes the completion record.
+struct FrameHost {
+    rtc_pf_done* done;           // device view of the mapped completion record
+    unsigned long long* ctr;     // device count of finished blocks (only grows)
+    unsigned long long target;   // the count that completes this launch (set by launch_frame)
+    unsigned long long seq;      // value of the record's seq for this call
+};
+
 // Device-visible addresses of the host ring for one rtc_run_loop call.
 struct LoopLaunch {
     const uint16_t* d_frames;
@@ -37,6 +55,7 @@ struct LoopLaunch {
     unsigned long long n_frames;
     int nslot;
     int n_bands;                 // >= 1 bands of pixel rows per frame
+    int l2_stream;               // stream the matrix with L2 evict_first whatever its size
 };
 
 struct rtc_handle {
@@ -79,7 +98,8 @@ struct rtc_handle {
     int* d_sl_loc = nullptr;
     float* d_s = nullptr;           // [kpad] slope vector, zero padded
     float* d_a = nullptr;           // [nact] integrator state
-    float* d_partial = nullptr;     // [dev_sms][nact] partial DM vectors, one per slice (scratch)
+    float* d_partial = nullptr;     // [2][dev_sms][nact] partial DM vectors, one per slice (scratch;
+                                    // the persistent loop alternates the halves frame by frame)
     uint16_t* d_frame = nullptr;    // [n_wfs][side][side] staging for host frames
     int* d_status = nullptr;        // device-side error word (RTC_ETIMEDOUT from bounded waits)
     unsigned long long* d_gridbar = nullptr;  // grid-barrier arrival counter (only grows)
@@ -109,6 +129,12 @@ struct rtc_handle {
     int ring_head = 3;                        // row of the newest vector
     float* d_spred = nullptr;                 // [kpad] predicted slopes, zero padded
     int* h_status = nullptr;        // pinned host mirror of d_status
+    // rtc_process_frame with pinned host buffers (allocated at its first such call)
+    rtc_pf_done* h_pf_done = nullptr;         // pinned mapped completion record
+    rtc_pf_done* d_pf_done = nullptr;         // its device view
+    unsigned long long* d_pf_ctr = nullptr;   // finished-block count of those launches
+    unsigned long long pf_arrivals = 0;       // block arrivals expected so far on d_pf_ctr
+    unsigned long long pf_seq = 0;            // calls made so far
 
     std::string err;
 };
@@ -133,8 +159,10 @@ cudaError_t launch_loop(rtc_handle* h, const LoopLaunch& ll, cudaStream_t st);
 // One frame through the fused kernel.  d_s_meas == nullptr: the plain path (slopes in
 // h->d_s).  Otherwise the predictor path: measured slopes into d_s_meas = ring row
 // `head` of h->d_ring, predicted slopes into h->d_spred, reconstruction from those.
+// fh (optional): the frame and d_dm_out are device views of mapped host memory, and
+// the launch writes fh->done when its commands are out.
 cudaError_t launch_frame(rtc_handle* h, const uint16_t* d_frame, float* d_dm_out, float* d_s_meas,
-                         int head, cudaStream_t st);
+                         int head, cudaStream_t st, FrameHost* fh = nullptr);
 cudaError_t launch_mvm_integrate(rtc_handle* h, const float* d_s, float* d_dm_out,
                                  cudaStream_t st);
 

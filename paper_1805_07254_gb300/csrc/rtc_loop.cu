@@ -161,6 +161,7 @@ extern "C" int rtc_run_loop(rtc_handle* h, const rtc_loop_config* cfg, rtc_stats
     ll.n_frames = n;
     ll.nslot = nslot;
     ll.n_bands = nb;
+    ll.l2_stream = cfg->matrix_l2 == 1 ? 1 : 0;
     LOOP_CUDA(launch_loop(h, ll, h->stream));
 
     // filler: frame k into slot k % nslot once frame k - nslot has left it

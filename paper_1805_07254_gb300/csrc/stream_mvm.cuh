@@ -125,6 +125,10 @@ __device__ __forceinline__ unsigned long long matrix_policy(int mode) {
         asm volatile("createpolicy.fractional.L2::evict_normal.b64 %0, 1.0;" : "=l"(p));
     return p;
 }
+// Bulk prefetch of global bytes into L2 (no shared memory, no completion).
+__device__ __forceinline__ void bulk_prefetch_l2(const void* src, uint32_t bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
+}
 __device__ __forceinline__ unsigned long long global_ns() {
     unsigned long long t;
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
@@ -388,14 +392,35 @@ __device__ __forceinline__ int tile_rows(const Args& g, int rb) {
     return g.R * (m < 1 ? 1 : m > kMaxRowsPerThread ? kMaxRowsPerThread : m);
 }
 
+// Source and size of tile t of the block (counted from the start of its first
+// slice); false past its last tile.
+__device__ __forceinline__ bool tile_src(const Args& g, const Plan& pl, int t, const unsigned char*& src,
+                                         uint32_t& bytes) {
+    for (int s = pl.sb0; s < pl.sb1; ++s) {
+        const int rb = g.sl.rowbytes[s];
+        const int tr = tile_rows(g, rb);
+        const int nt = (g.nact + tr - 1) / tr;
+        if (t < nt) {
+            const int row0 = t * tr;
+            src = g.M + g.sl.off[s] + static_cast<size_t>(row0) * rb;
+            bytes = (static_cast<uint32_t>(min(tr, g.nact - row0)) * rb + 15u) & ~15u;
+            return true;
+        }
+        t -= nt;
+    }
+    return false;
+}
+
 // One producer thread: stream the block's slices tile by tile into the ring.
 // tl0: the running tile count at entry (barrier phases continue across calls, e.g.
 // frame after frame in a persistent kernel); returns the count at exit.  drain: wait
 // for the last copies to land before returning (a block must not exit with copies
 // in flight).  hold > 0: after the first `hold` tiles, wait until the consumers set
-// sh.release (the latency-critical pixel loads then do not queue behind the stream).
+// sh.release (the latency-critical pixel loads then do not queue behind the
+// stream).  hold_l2: tiles prefetched into L2 right before that wait (a long wait,
+// such as the predictor's, then leaves the HBM streaming).
 __device__ __forceinline__ int produce(const Args& g, const Plan& pl, Shared& sh, int tl0 = 0,
-                                       bool drain = true, int hold = 0) {
+                                       bool drain = true, int hold = 0, int hold_l2 = 0) {
     int tl = tl0;
     bool ok = true;
     const unsigned long long policy = matrix_policy(g.l2_policy);
@@ -404,9 +429,16 @@ __device__ __forceinline__ int produce(const Args& g, const Plan& pl, Shared& sh
         const int rb = g.sl.rowbytes[s];
         const int tr = tile_rows(g, rb);
         for (int row0 = 0; row0 < g.nact; row0 += tr, ++tl) {
-            if (hold > 0 && tl - tl0 == hold && !wait_flag(&sh.release, &sh.abort_flag)) {
-                ok = false;
-                break;
+            if (hold > 0 && tl - tl0 == hold) {
+                for (int j = 0; j < hold_l2; ++j) {
+                    const unsigned char* psrc;
+                    uint32_t pbytes;
+                    if (tile_src(g, pl, hold + j, psrc, pbytes)) bulk_prefetch_l2(psrc, pbytes);
+                }
+                if (!wait_flag(&sh.release, &sh.abort_flag)) {
+                    ok = false;
+                    break;
+                }
             }
             const int st = tl % g.nst;
             const int use = tl / g.nst;

@@ -44,7 +44,8 @@ class RtcLoopConfig(C.Structure):
     _fields_ = [("n_frames", C.c_uint64), ("rate_hz", C.c_double), ("source", SOURCE_FN),
                 ("source_user", C.c_void_p), ("preload", C.c_void_p), ("n_preload", C.c_int32),
                 ("sink", SINK_FN), ("sink_user", C.c_void_p), ("e2e_ns", C.c_void_p),
-                ("dev_ns", C.c_void_p), ("n_bands", C.c_int32), ("band_interval_us", C.c_double)]
+                ("dev_ns", C.c_void_p), ("n_bands", C.c_int32), ("band_interval_us", C.c_double),
+                ("matrix_l2", C.c_int32)]
 
 
 class RtcStats(C.Structure):
@@ -289,21 +290,24 @@ class Rtc:
                                                     _stream_ptr(stream)))
 
     def run_loop(self, n_frames: int, rate_hz: float = 0.0, frames=None, source=None, sink=None,
-                 record: bool = True, bands: int = 0, band_interval_us: float = 0.0):
+                 record: bool = True, bands: int = 0, band_interval_us: float = 0.0,
+                 matrix_l2: int = 0):
         """Persistent real-time loop (rtc_run_loop).
 
         frames: uint16 array (n, [n_wfs,] H, W), 1 <= n <= 8, cycled; or source(k) -> frame
         array for frame k (None stops the loop).  sink(k, dm) receives each frame's DM
         commands (a float32 array valid during the call).  bands > 1 publishes each
         frame in that many bands of pixel rows, band_interval_us apart (a rolling
-        readout).  Returns (stats dict, e2e_ns, dev_ns) with per-frame latencies when
-        record is true."""
+        readout).  matrix_l2=1 streams the matrix with L2 evict_first whatever its size.
+        Returns (stats dict, e2e_ns, dev_ns) with per-frame latencies when record is
+        true."""
         n_frames = int(n_frames)
         cfg = RtcLoopConfig()
         cfg.n_frames = n_frames
         cfg.rate_hz = float(rate_hz)
         cfg.n_bands = int(bands)
         cfg.band_interval_us = float(band_interval_us)
+        cfg.matrix_l2 = int(matrix_l2)
         keep = []
         if source is not None:
             nbytes = [None]

@@ -237,3 +237,33 @@ def test_fused_frame_kernel_equals_stage_kernels(store):
         r2.synchronize(st)
         assert torch.equal(s1, s2)
         assert torch.equal(dm1, dm2)
+
+
+@pytest.mark.parametrize("cfg_name,store,pred", [("tiny", "f32", False), ("elt", "f32", False),
+                                                 ("elt", "bf16", True), ("elt", "fp8", False)])
+def test_pinned_host_buffers_give_the_copy_path_results(cfg_name, store, pred):
+    """rtc_process_frame with pinned host buffers reads the frame and writes the DM
+    commands over the host link (no copies); with pageable buffers it copies.  Both give
+    the same slopes and commands bit for bit, frame after frame, and match the oracle."""
+    from synth.mlp_init import init_mlp_params, flatten
+    cfg = synth.CONFIGS[cfg_name]()
+    frames, _ = synth.make_frames(cfg, 0, 6)
+    r1, oracle, *_ = make_pair(cfg, store=store)
+    r2, *_ = make_pair(cfg, store=store)
+    if pred:
+        for r in (r1, r2):
+            r.load_predictor(flatten(init_mlp_params(3)), 0.3)
+            r.set_predictor(True)
+    pin_frame = torch.empty(frames[0].shape, dtype=torch.uint16).pin_memory()
+    pin_dm = torch.empty(cfg.nact, dtype=torch.float32).pin_memory()
+    pin_s = torch.empty(cfg.nslopes, dtype=torch.float32).pin_memory()
+    for k in range(frames.shape[0]):
+        pin_frame.copy_(frames[k])
+        r1.process_frame(pin_frame, dm_out=pin_dm, slopes_out=pin_s)
+        dm2, s2 = r2.process_frame(frames[k].numpy(), want_slopes=True)
+        np.testing.assert_array_equal(pin_dm.numpy(), dm2)
+        np.testing.assert_array_equal(pin_s.numpy(), s2)
+        if not pred:
+            a_ref, s_ref = oracle.step(frames[k].numpy())
+            assert np.max(np.abs(s2 - s_ref)) <= SLOPE_TOL
+            assert rel_rms(dm2, a_ref) <= DM_TOL
