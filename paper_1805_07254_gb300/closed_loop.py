@@ -20,7 +20,9 @@ slopes, commands and mirror never leave the device.  The scores are the RMS of
 the true residual slopes the WFS sees and the RMS of the residual wavefront over
 the pupil (piston removed), against the turbulence alone.  ``evaluate`` compares
 the plain integrator with the integrator fed by the learned slope predictor,
-trained on the residual slopes of closed-loop runs with other turbulence.
+trained on the residual slopes of closed-loop runs with other turbulence;
+``evaluate_pol`` compares it with pseudo-open-loop predictive control, the
+predictor forecasting the turbulence's own slopes (``PolController``).
 """
 from __future__ import annotations
 
@@ -160,6 +162,119 @@ def library_step(r: Rtc, device, slopes: torch.Tensor | None = None):
     return step
 
 
+class PolController:
+    """Pseudo-open-loop (POL) predictive control with the library's kernels.
+
+    The measured slopes s(k) = s_turb(k) - D a(k-1) plus the mirror's own slopes
+    give the POL slopes p(k) = s(k) + D a(k-1), an estimate of the turbulence alone
+    that does not depend on the control law.  The learned predictor, trained on POL
+    sequences, forecasts p(k+1) from p(k) .. p(k-3); the integrator is then fed the
+    residual the new commands will meet, e(k) = p_hat(k+1) - D a(k-1), so that
+    a(k) = leak a(k-1) + g R e(k).  With the prediction replaced by p(k) itself this
+    is exactly the plain integrator (e = s).  Per frame: rtc_centroid_async (slopes),
+    rtc_mvm_integrate_noalloc with D (the POL slopes, p = s + D a), rtc_mlp_predict_seq
+    (the forecast) and rtc_reconstruct_async (integrator)."""
+
+    def __init__(self, r: Rtc, D: torch.Tensor, params, sigma: float, cfg, device, predict: bool = True):
+        from .rtc import Mlp
+        self.r, self.dev, self.cfg, self.sigma = r, device, cfg, float(sigma)
+        self.ns, self.na = D.shape
+        self.kpad_a = (self.na + 15) // 16 * 16
+        self.D = torch.zeros((self.ns, self.kpad_a), device=device)
+        self.D[:, :self.na] = D
+        self.a_pad = torch.zeros(self.kpad_a, device=device)       # a(k-1), zero padded
+        self.s = torch.zeros(self.ns, device=device)
+        self.pol = torch.zeros(self.ns, device=device)
+        self.hist = torch.zeros((5, self.ns), device=device)        # p(k-3) .. p(k), spare row
+        self.out = torch.zeros((5, self.ns), device=device)
+        self.e = torch.zeros(self.ns, device=device)
+        self.d_dm = torch.zeros(cfg.nact, device=device)
+        self.m = None
+        if predict:
+            self.m = Mlp(device=device.index or 0, params=params)
+            self.m.set_geometry(cfg.subaps, cfg.nsub)
+        self.k = 0
+
+    def close(self):
+        if self.m is not None:
+            self.m.close()
+
+    def step(self, frame):
+        from .rtc import mvm_integrate_noalloc
+        st = torch.cuda.current_stream(self.dev)
+        self.r.centroid_async(frame, self.s, stream=st)
+        # p = s + D a(k-1): the allocation-free MVM with leak 1 and gain 1 on p := s
+        self.pol.copy_(self.s)
+        mvm_integrate_noalloc(self.D, "f32", None, self.ns, self.kpad_a, self.a_pad, self.pol, None,
+                              1.0, 1.0, 1, stream=st)
+        self.hist[:4] = self.hist[1:].clone()
+        self.hist[3] = self.pol
+        if self.m is not None and self.k >= 3:
+            self.m.predict_seq(self.hist, self.sigma, self.out, stream=st)
+            p_hat = self.out[4]
+        else:
+            p_hat = self.pol
+        # e = p_hat - D a(k-1) = p_hat - (p - s)
+        torch.add(p_hat - self.pol, self.s, out=self.e)
+        self.r.reconstruct_async(self.e, self.d_dm, stream=st)
+        self.a_pad[:self.na] = self.d_dm
+        self.k += 1
+        return self.d_dm
+
+
+def evaluate_pol(cfg=None, train_frames: int = 20_000, test_frames: int = 5_000, seed: int = 0,
+                 steps: int | None = None, gains=(0.4, 0.7, 1.0), device="cuda:0",
+                 alpha_rel: float = 1e-3) -> dict:
+    """Integrator against POL predictive control in the closed loop.  The predictor
+    is trained on the POL slopes of an integrator loop through turbulence with other
+    seeds; every law is scored on the same held-out turbulence and noise."""
+    from .predictor import train_on
+    cfg = cfg or synth.elt_scao()
+    dev = torch.device(device)
+    nl = len(cfg.screen_seeds)
+    train_seeds = tuple(2000 + 10 * seed + i for i in range(nl))
+    test_seeds = tuple(6000 + 10 * seed + i for i in range(nl))
+
+    sim = ClosedLoopSim(cfg, dev, train_seeds, noise_seed=7100 + seed, alpha_rel=alpha_rel)
+    r = sim.controller()
+    ctl = PolController(r, sim.D, None, 1.0, cfg, dev, predict=False)
+    P = torch.zeros((train_frames, cfg.nslopes), device=dev)
+
+    def record(frame):
+        out = ctl.step(frame)
+        P[ctl.k - 1] = ctl.pol
+        return out
+    sim.run(record, train_frames)
+    r.close()
+    m, sigma, n_steps, loss, train_s = train_on(P, cfg, steps, seed=seed)
+    params = m.get_params()
+    m.close()
+    del P
+
+    test = ClosedLoopSim(cfg, dev, test_seeds, noise_seed=8100 + seed, alpha_rel=alpha_rel)
+    out = {"config": cfg.name, "alpha_rel": alpha_rel, "train_frames": train_frames,
+           "test_frames": test_frames, "training_steps": n_steps, "final_loss": loss,
+           "train_seconds": round(train_s, 2), "sigma_px": sigma, "laws": {}}
+    for g in gains:
+        for predict in (False, True):
+            r = test.controller()
+            r.set_gain(g, cfg.leak)
+            ctl = PolController(r, test.D, params, sigma, cfg, dev, predict=predict)
+            sc = test.run(ctl.step, test_frames)
+            ctl.close()
+            r.close()
+            out["laws"][f"{'pol_predictor' if predict else 'integrator'}_g{g}"] = {
+                "phase_nm": sc.phase_rms_nm, "slope_rms_px": sc.slope_rms_px, "frames": sc.frames}
+            out["open_loop_phase_nm"] = sc.open_phase_rms_nm
+    torch.cuda.synchronize(dev)
+    best_i = min((v["phase_nm"], k) for k, v in out["laws"].items() if k.startswith("integrator"))
+    best_p = min((v["phase_nm"], k) for k, v in out["laws"].items() if k.startswith("pol_predictor"))
+    out["best_integrator"] = {"law": best_i[1], "phase_nm": best_i[0]}
+    out["best_pol_predictor"] = {"law": best_p[1], "phase_nm": best_p[0]}
+    out["keep_predictor"] = bool(best_p[0] < best_i[0])
+    return out
+
+
 def evaluate(cfg=None, train_frames: int = 20_000, test_frames: int = 5_000, seed: int = 0,
              store: str = "f32", steps: int | None = None, device="cuda:0",
              alpha_rel: float = 1e-3) -> dict:
@@ -219,7 +334,13 @@ def main(argv=None):
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--alpha", type=float, default=1e-3, help="reconstructor regularisation, "
                     "relative to the mean diagonal of D^T D")
+    ap.add_argument("--pol", action="store_true", help="pseudo-open-loop predictive control "
+                    "against the integrator, at gains 0.4, 0.7 and 1.0")
     a = ap.parse_args(argv)
+    if a.pol:
+        print(json.dumps(evaluate_pol(synth.CONFIGS[a.config](), a.train_frames, a.test_frames, a.seed,
+                                      a.steps, alpha_rel=a.alpha)))
+        return
     print(json.dumps(evaluate(synth.CONFIGS[a.config](), a.train_frames, a.test_frames, a.seed,
                               a.store, a.steps, alpha_rel=a.alpha)))
 

@@ -206,14 +206,14 @@ __global__ void row_scale_kernel(const float* __restrict__ src, int ncol, float*
 // One row per block: FP32 column c -> its slice's row in the stored type.
 template <int DT>
 __global__ void layout_f32_kernel(const float* __restrict__ src, int ncol, const int2* __restrict__ colmap,
-                                  const long long* __restrict__ off, const int* __restrict__ rowbytes,
+                                  const long long* __restrict__ off, const int* __restrict__ rowbytes, int plane,
                                   const float* __restrict__ scale, unsigned char* __restrict__ dst) {
-    const int row = blockIdx.x;
+    const int row = blockIdx.x, nact = gridDim.x;
     const float sc = RowScaled<DT>::v ? scale[row] : 1.f;
     for (int c = threadIdx.x; c < ncol; c += blockDim.x) {
         const int2 sj = colmap[c];
-        unsigned char* p = dst + off[sj.x] + static_cast<size_t>(row) * rowbytes[sj.x] +
-                           static_cast<size_t>(sj.y) * Esize<DT>::v;
+        unsigned char* p =
+            dst + rtc_mvm::slice_elem_offset(off[sj.x], rowbytes[sj.x], nact, row, sj.y * Esize<DT>::v, plane);
         const float v = src[static_cast<size_t>(row) * ncol + c];
         if (DT == RTC_F32) *reinterpret_cast<float*>(p) = v;
         else if (DT == RTC_BF16) *reinterpret_cast<__nv_bfloat16*>(p) = __float2bfloat16_rn(v);
@@ -225,12 +225,11 @@ __global__ void layout_f32_kernel(const float* __restrict__ src, int ncol, const
 // One row per block: an element of esize bytes, already in the stored type.
 __global__ void layout_raw_kernel(const unsigned char* __restrict__ src, int ncol, int esize,
                                   const int2* __restrict__ colmap, const long long* __restrict__ off,
-                                  const int* __restrict__ rowbytes, unsigned char* __restrict__ dst) {
-    const int row = blockIdx.x;
+                                  const int* __restrict__ rowbytes, int plane, unsigned char* __restrict__ dst) {
+    const int row = blockIdx.x, nact = gridDim.x;
     for (int c = threadIdx.x; c < ncol; c += blockDim.x) {
         const int2 sj = colmap[c];
-        unsigned char* p = dst + off[sj.x] + static_cast<size_t>(row) * rowbytes[sj.x] +
-                           static_cast<size_t>(sj.y) * esize;
+        unsigned char* p = dst + rtc_mvm::slice_elem_offset(off[sj.x], rowbytes[sj.x], nact, row, sj.y * esize, plane);
         const unsigned char* q = src + (static_cast<size_t>(row) * ncol + c) * esize;
         for (int b = 0; b < esize; ++b) p[b] = q[b];
     }
@@ -238,16 +237,16 @@ __global__ void layout_raw_kernel(const unsigned char* __restrict__ src, int nco
 
 __global__ void relayout_kernel(const unsigned char* __restrict__ src, const int2* __restrict__ src_map,
                                 const long long* __restrict__ src_off, const int* __restrict__ src_rb,
-                                int ncol, int esize, const int2* __restrict__ dst_map,
+                                int ncol, int esize, int src_plane, int dst_plane, const int2* __restrict__ dst_map,
                                 const long long* __restrict__ dst_off, const int* __restrict__ dst_rb,
                                 unsigned char* __restrict__ dst) {
-    const int row = blockIdx.x;
+    const int row = blockIdx.x, nact = gridDim.x;
     for (int c = threadIdx.x; c < ncol; c += blockDim.x) {
         const int2 a = src_map[c], b = dst_map[c];
-        const unsigned char* q = src + src_off[a.x] + static_cast<size_t>(row) * src_rb[a.x] +
-                                 static_cast<size_t>(a.y) * esize;
-        unsigned char* p = dst + dst_off[b.x] + static_cast<size_t>(row) * dst_rb[b.x] +
-                           static_cast<size_t>(b.y) * esize;
+        const unsigned char* q =
+            src + rtc_mvm::slice_elem_offset(src_off[a.x], src_rb[a.x], nact, row, a.y * esize, src_plane);
+        unsigned char* p =
+            dst + rtc_mvm::slice_elem_offset(dst_off[b.x], dst_rb[b.x], nact, row, b.y * esize, dst_plane);
         for (int k = 0; k < esize; ++k) p[k] = q[k];
     }
 }
@@ -290,32 +289,32 @@ cudaError_t launch_mvm_raw(int store, const void* d_M, const float* d_scale, int
 }
 
 cudaError_t launch_layout(int src, int store, const void* d_src, int nact, int ncol,
-                          const int2* d_colmap, const long long* d_off, const int* d_rowbytes,
+                          const int2* d_colmap, const long long* d_off, const int* d_rowbytes, int plane,
                           float* d_scale, void* d_dst, cudaStream_t st) {
     if (nact <= 0 || ncol <= 0) return cudaSuccess;
     unsigned char* dst = static_cast<unsigned char*>(d_dst);
     if (src == store) {
         const int esize = store == RTC_F32 ? 4 : (store == RTC_BF16 || store == RTC_F16) ? 2 : 1;
         layout_raw_kernel<<<nact, 256, 0, st>>>(static_cast<const unsigned char*>(d_src), ncol, esize,
-                                                d_colmap, d_off, d_rowbytes, dst);
+                                                d_colmap, d_off, d_rowbytes, plane, dst);
         return cudaGetLastError();
     }
     if (src != RTC_F32) return cudaErrorInvalidValue;
     const float* f = static_cast<const float*>(d_src);
     switch (store) {
         case RTC_BF16:
-            layout_f32_kernel<RTC_BF16><<<nact, 256, 0, st>>>(f, ncol, d_colmap, d_off, d_rowbytes, d_scale, dst);
+            layout_f32_kernel<RTC_BF16><<<nact, 256, 0, st>>>(f, ncol, d_colmap, d_off, d_rowbytes, plane, d_scale, dst);
             break;
         case RTC_F16:
-            layout_f32_kernel<RTC_F16><<<nact, 256, 0, st>>>(f, ncol, d_colmap, d_off, d_rowbytes, d_scale, dst);
+            layout_f32_kernel<RTC_F16><<<nact, 256, 0, st>>>(f, ncol, d_colmap, d_off, d_rowbytes, plane, d_scale, dst);
             break;
         case RTC_FP8_E4M3:
             row_scale_kernel<RTC_FP8_E4M3><<<nact, 256, 0, st>>>(f, ncol, d_scale);
-            layout_f32_kernel<RTC_FP8_E4M3><<<nact, 256, 0, st>>>(f, ncol, d_colmap, d_off, d_rowbytes, d_scale, dst);
+            layout_f32_kernel<RTC_FP8_E4M3><<<nact, 256, 0, st>>>(f, ncol, d_colmap, d_off, d_rowbytes, plane, d_scale, dst);
             break;
         case RTC_INT8:
             row_scale_kernel<RTC_INT8><<<nact, 256, 0, st>>>(f, ncol, d_scale);
-            layout_f32_kernel<RTC_INT8><<<nact, 256, 0, st>>>(f, ncol, d_colmap, d_off, d_rowbytes, d_scale, dst);
+            layout_f32_kernel<RTC_INT8><<<nact, 256, 0, st>>>(f, ncol, d_colmap, d_off, d_rowbytes, plane, d_scale, dst);
             break;
         default:
             return cudaErrorInvalidValue;
@@ -323,12 +322,13 @@ cudaError_t launch_layout(int src, int store, const void* d_src, int nact, int n
     return cudaGetLastError();
 }
 
-cudaError_t launch_relayout(int esize, const void* d_old, const int2* d_old_colmap, const long long* d_old_off,
-                            const int* d_old_rowbytes, int nact, int ncol, const int2* d_new_colmap,
-                            const long long* d_new_off, const int* d_new_rowbytes, void* d_new, cudaStream_t st) {
+cudaError_t launch_relayout(int esize, int old_plane, int new_plane, const void* d_old, const int2* d_old_colmap,
+                            const long long* d_old_off, const int* d_old_rowbytes, int nact, int ncol,
+                            const int2* d_new_colmap, const long long* d_new_off, const int* d_new_rowbytes,
+                            void* d_new, cudaStream_t st) {
     if (nact <= 0 || ncol <= 0) return cudaSuccess;
     relayout_kernel<<<nact, 256, 0, st>>>(static_cast<const unsigned char*>(d_old), d_old_colmap, d_old_off,
-                                          d_old_rowbytes, ncol, esize, d_new_colmap, d_new_off, d_new_rowbytes,
-                                          static_cast<unsigned char*>(d_new));
+                                          d_old_rowbytes, ncol, esize, old_plane, new_plane, d_new_colmap, d_new_off,
+                                          d_new_rowbytes, static_cast<unsigned char*>(d_new));
     return cudaGetLastError();
 }

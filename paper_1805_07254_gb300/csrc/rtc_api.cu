@@ -131,6 +131,14 @@ void cut_slices(rtc_handle* h, const std::vector<int>& g0, int esz, std::vector<
     }
     h->sl_loc[S] = loc;
     h->m_bytes = off;
+    // 1-byte stores take the plane layout when one lane per row holds (two ring
+    // stages of kConsumers rows leave a generous margin of shared memory): their
+    // rows then load as 16-byte units (measured: FP8 frame 21.0 against 22.5 us on
+    // ELT; 2-byte stores, which keep up with the HBM anyway, gained nothing)
+    int max_rb = 0;
+    for (int s = 0; s < S; ++s) max_rb = std::max(max_rb, h->sl_rowbytes[s]);
+    h->sl_plane = esz == 1 && 2 * static_cast<long long>(rtc_mvm::kConsumers) * max_rb + (64 << 10) <=
+                                  static_cast<long long>(rtc_mvm::kDynSmemBudget);
     const int nv = h->n_valid, nt = nv * h->cfg.n_wfs;
     std::vector<int> slice_of(nt);
     for (int s = 0; s < S; ++s)
@@ -567,7 +575,7 @@ int rtc_load_cmat(rtc_handle* h, const void* M, int32_t nact, int32_t nslopes, i
     if (e == cudaSuccess) e = cudaMemcpy(d_colmap, colmap.data(), nslopes * sizeof(int2), cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
         e = launch_layout(src, store, staging, nact, nslopes, d_colmap, h->d_sl_off, h->d_sl_rowbytes,
-                          h->d_scale, h->d_M, h->stream);
+                          h->sl_plane ? 1 : 0, h->d_scale, h->d_M, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     cudaFree(staging);
     cudaFree(d_colmap);
@@ -591,6 +599,7 @@ int rtc_set_readout(rtc_handle* h, int32_t n_bands, double band_interval_us) {
     const int nact = h->cfg.nact, ncol = h->nslopes;
     std::vector<int2> old_map, new_map;
     cut_slices(h, h->sl_g0, esz, old_map);                  // the present cut's column map
+    const int old_plane = h->sl_plane ? 1 : 0;
     const std::vector<int> g0 = slice_bounds(h, esz);
     void* old_M = h->d_M;
     long long* old_off = h->d_sl_off;
@@ -613,8 +622,8 @@ int rtc_set_readout(rtc_handle* h, int32_t n_bands, double band_interval_us) {
     if (e == cudaSuccess)
         e = cudaMemcpy(d_maps + ncol, new_map.data(), ncol * sizeof(int2), cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
-        e = launch_relayout(esz, old_M, d_maps, old_off, old_rb, nact, ncol, d_maps + ncol, h->d_sl_off,
-                            h->d_sl_rowbytes, h->d_M, h->stream);
+        e = launch_relayout(esz, old_plane, h->sl_plane ? 1 : 0, old_M, d_maps, old_off, old_rb, nact, ncol, d_maps + ncol,
+                            h->d_sl_off, h->d_sl_rowbytes, h->d_M, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (d_maps) cudaFree(d_maps);
     cudaFree(old_M);

@@ -92,6 +92,7 @@ struct rtc_handle {
     std::vector<int> sl_g0;         // [S + 1] first subaperture of each slice
     std::vector<int> sl_loc;        // [S + 1] float offset of each slice's slopes in a local vector
     bool sl_equal = false;          // sl_g0[s] == nt * s / S for every s
+    bool sl_plane = false;          // slices stored in the plane layout (1- and 2-byte stores)
     long long* d_sl_off = nullptr;
     int* d_sl_rowbytes = nullptr;
     int* d_sl_g0 = nullptr;
@@ -178,14 +179,15 @@ cudaError_t launch_mvm_raw(int store, const void* d_M, const float* d_scale, int
 // local column colmap[c].y.  From FP32, the FP8 / INT8 row scales are computed
 // into d_scale first.
 cudaError_t launch_layout(int src, int store, const void* d_src, int nact, int ncol,
-                          const int2* d_colmap, const long long* d_off, const int* d_rowbytes,
+                          const int2* d_colmap, const long long* d_off, const int* d_rowbytes, int plane,
                           float* d_scale, void* d_dst, cudaStream_t st);
 
 // Move a matrix between two slice layouts of the same store (esize bytes per
 // entry): column c from (old_colmap[c]) to (new_colmap[c]).
-cudaError_t launch_relayout(int esize, const void* d_old, const int2* d_old_colmap, const long long* d_old_off,
-                            const int* d_old_rowbytes, int nact, int ncol, const int2* d_new_colmap,
-                            const long long* d_new_off, const int* d_new_rowbytes, void* d_new, cudaStream_t st);
+cudaError_t launch_relayout(int esize, int old_plane, int new_plane, const void* d_old, const int2* d_old_colmap,
+                            const long long* d_old_off, const int* d_old_rowbytes, int nact, int ncol,
+                            const int2* d_new_colmap, const long long* d_new_off, const int* d_new_rowbytes,
+                            void* d_new, cudaStream_t st);
 
 // Read and clear the device status word after `st` drains (RTC_OK or the recorded
 // error, which also restarts the grid-barrier count); set the handle's message.

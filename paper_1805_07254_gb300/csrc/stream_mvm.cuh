@@ -161,6 +161,22 @@ __host__ __device__ __forceinline__ int row_unit(int rb) {
     if (rb % 4 == 0 && (rb / 4) % 2 == 1) return 4;
     return 0;
 }
+// Byte offset of byte cb of row `row` of a slice (at byte off, rb bytes per row,
+// nact rows).  Row-major, or in the plane layout: rows in groups of 32, and within a
+// group the rows' first 16-byte units, then their second ones, ..., then their
+// (rb % 16)-byte tails.  A group of ng rows takes ng * rb bytes either way, so tiles
+// of whole groups are the same byte ranges in both layouts.
+__host__ __device__ __forceinline__ size_t slice_elem_offset(long long off, int rb, int nact, int row, int cb,
+                                                             int plane) {
+    if (!plane) return static_cast<size_t>(off) + static_cast<size_t>(row) * rb + cb;
+    const int g0 = row & ~31;
+    const int ng = nact - g0 < 32 ? nact - g0 : 32;
+    const int li = row - g0, q = rb >> 4, t = rb & 15, k = cb >> 4;
+    const size_t base = static_cast<size_t>(off) + static_cast<size_t>(g0) * rb;
+    if (k < q) return base + static_cast<size_t>(k) * ng * 16 + li * 16 + (cb & 15);
+    return base + static_cast<size_t>(q) * ng * 16 + static_cast<size_t>(li) * t + (cb - 16 * q);
+}
+
 __device__ __forceinline__ void consumer_sync() {          // all consumer warps
     asm volatile("bar.sync 1, %0;" ::"n"(kConsumers) : "memory");
 }
@@ -269,6 +285,7 @@ struct Args {
     int region;              // shared scratch bytes of a fused phase (before the slopes)
     int loc_floats;          // floats of the largest block-local slope vector
     int row_floats;          // rows a block reduces, at most
+    int plane;               // slices in the plane layout (T = 1; see slice_elem_offset)
     const float* s;          // stand-alone reconstruction: the full slope vector (else unused)
     const float* scale;      // [nact] row scales (FP8, INT8)
     float* partial;          // [S][nact] partial DM vectors
@@ -619,6 +636,77 @@ __device__ __forceinline__ int consume_slice(const Args& g, const Plan& pl, Shar
     return tile;
 }
 
+// The tiles of one slice in the plane layout (T = 1, R = kConsumers rows a tile step):
+// warp w takes rows 32 w .. 32 w + 31 of each step, one group, so every 16-byte load
+// of the warp reads 512 consecutive bytes, and the (rb % 16)-byte tails follow the
+// group's units.  Rows are taken two at a time, sharing each unit's slope loads.
+// Each row's terms are added in element order, the order of the row-major form.
+template <int DT>
+__device__ __forceinline__ int consume_slice_plane(const Args& g, const Plan& pl, Shared& sh, int tid,
+                                                   int tile, int s, int rb, int lo) {
+    constexpr int E16 = 16 / Esize<DT>::v;                   // elements per 16-byte unit
+    constexpr int EPW = 4 / Esize<DT>::v;                    // elements per word
+    const int R = g.R, nact = g.nact, nst = g.nst, stage_bytes = g.stage_bytes;
+    const int lane = tid & 31;
+    const int q = rb >> 4, tb = rb & 15;
+    const float* sv = pl.loc + lo;
+    const float* st_tail = sv + q * E16;
+    float* out = g.partial + static_cast<size_t>(s) * nact;
+    const int tr = tile_rows(g, rb);
+    for (int row0 = 0; row0 < nact; row0 += tr, ++tile) {
+        const int st = tile % nst;
+        const bool ok = __all_sync(0xffffffffu, wait_phase(smem_addr(&sh.full_bar[st]),
+                                                            (tile / nst) & 1, &sh.abort_flag));
+        if (!ok) {
+            if (lane == 0 && !sh.abort_flag) {
+                atomicExch(g.status, RTC_ETIMEDOUT);
+                sh.abort_flag = 1;
+            }
+            continue;     // skip the work but keep reaching the block's barriers
+        }
+        const uint32_t stage = pl.ring + st * stage_bytes;
+        const int iters = (min(tr, nact - row0) + R - 1) / R;
+        for (int i = 0; i < iters; i += 2) {
+            const int ra = tid + i * R, rbw = ra + R;
+            const bool va = row0 + ra < nact;
+            const bool vb = i + 1 < iters && row0 + rbw < nact;
+            const int ga = ra & ~31, gb = rbw & ~31;
+            const int na = min(32, nact - row0 - ga), nb = min(32, nact - row0 - gb);
+            const uint32_t pa = stage + ga * rb + lane * 16, pb = stage + gb * rb + lane * 16;
+            float acc0 = 0.f, acc1 = 0.f;
+#pragma unroll 2
+            for (int k = 0; k < q; ++k) {
+                float r[E16];
+                load_unit<E16>(sv + k * E16, r);
+                if (va) acc0 = unit_dot<DT, 16>(acc0, pa + k * na * 16, r);
+                if (vb) acc1 = unit_dot<DT, 16>(acc1, pb + k * nb * 16, r);
+            }
+            if (tb) {
+                const uint32_t ta = stage + ga * rb + q * na * 16 + lane * tb;
+                const uint32_t tbb = stage + gb * rb + q * nb * 16 + lane * tb;
+                if (tb == 8) {
+                    float r[2 * EPW];
+                    load_unit<2 * EPW>(st_tail, r);
+                    if (va) acc0 = unit_dot<DT, 8>(acc0, ta, r);
+                    if (vb) acc1 = unit_dot<DT, 8>(acc1, tbb, r);
+                } else {
+                    for (int w = 0; w < tb / 4; ++w) {
+                        float r[EPW];
+                        load_unit<EPW>(st_tail + w * EPW, r);
+                        if (va) acc0 = word_dot<DT>(acc0, lds32(ta + 4 * w), r);
+                        if (vb) acc1 = word_dot<DT>(acc1, lds32(tbb + 4 * w), r);
+                    }
+                }
+            }
+            if (va) out[row0 + ra] = acc0;
+            if (vb) out[row0 + rbw] = acc1;
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(smem_addr(&sh.empty_bar[st]));
+    }
+    return tile;
+}
+
 // The consumer warps: every tile of the block's slices, one partial vector per
 // slice (partial[s][row] = the row's dot product with the slice's slopes, in unit
 // order).  tile0: the running tile count at entry; returns the count at exit.  The
@@ -634,7 +722,8 @@ __device__ __forceinline__ int consume(const Args& g, const Plan& pl, Shared& sh
             lo_next = __ldg(g.sl.loc + s + 1) - pl.loc0;
         }
         const int u = row_unit(rb);
-        if (u == 16) tile = consume_slice<DT, 16>(g, pl, sh, tid, tile, s, rb, lo);
+        if (g.plane) tile = consume_slice_plane<DT>(g, pl, sh, tid, tile, s, rb, lo);
+        else if (u == 16) tile = consume_slice<DT, 16>(g, pl, sh, tid, tile, s, rb, lo);
         else if (u == 8) tile = consume_slice<DT, 8>(g, pl, sh, tid, tile, s, rb, lo);
         else tile = consume_slice<DT, 4>(g, pl, sh, tid, tile, s, rb, lo);
         rb = rb_next;
@@ -755,7 +844,7 @@ inline Launch plan_launch(const rtc_handle* h, size_t min_region = 0) {
     L.nst = static_cast<int>(fit < static_cast<size_t>(kMaxStages) ? fit : kMaxStages);
     L.smem = static_cast<size_t>(L.nst) * L.stage_bytes + extra;
     L.ok = L.nst >= 2 && L.loc_floats <= kMaxLocalFloats && L.row_floats <= kMaxRowFloats &&
-           S <= kMaxSlices && L.smem <= kDynSmemBudget;
+           S <= kMaxSlices && L.smem <= kDynSmemBudget && (!h->sl_plane || L.T == 1);
     return L;
 }
 
@@ -772,6 +861,7 @@ inline Args make_args(const rtc_handle* h, const float* d_s, float* d_dm_out, co
     g.nst = L.nst;
     g.l2_policy = h->m_bytes <= kL2KeepBytes ? kL2Normal : kL2Stream;
     g.region = static_cast<int>(L.region);
+    g.plane = h->sl_plane ? 1 : 0;
     g.loc_floats = L.loc_floats;
     g.row_floats = L.row_floats;
     g.s = d_s;

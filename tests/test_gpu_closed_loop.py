@@ -73,3 +73,45 @@ def test_predictor_comparison_runs_and_reports():
         assert math.isfinite(res[k]) and res[k] > 0
     assert res["integrator_phase_nm"] < res["open_loop_phase_nm"]
     assert res["keep_predictor"] == (res["predictor_phase_nm"] < res["integrator_phase_nm"])
+
+
+def test_pol_controller_without_prediction_is_the_integrator():
+    """The pseudo-open-loop controller with the forecast replaced by the present POL
+    slopes feeds the integrator e = s, so it gives the plain integrator's commands bit
+    for bit; its POL slopes p = s + D a(k-1), computed by the allocation-free MVM,
+    match the same product in FP64."""
+    from paper_1805_07254_gb300.closed_loop import ClosedLoopSim, PolController, library_step
+    cfg = synth.tiny_scao()
+    dev = torch.device("cuda:0")
+    sim = ClosedLoopSim(cfg, dev)
+    r1, r2 = sim.controller(), sim.controller()
+    ctl = PolController(r2, sim.D, None, 1.0, cfg, dev, predict=False)
+    lib = library_step(r1, dev)
+    D64 = sim.D.double().cpu().numpy()
+    worst = [0.0]
+
+    def step(frame):
+        a_prev = ctl.a_pad[:cfg.nact].double().cpu().numpy()
+        a1 = lib(frame).clone()
+        a2 = ctl.step(frame)
+        assert torch.equal(a1, a2)
+        ref = ctl.s.double().cpu().numpy() + D64 @ a_prev
+        worst[0] = max(worst[0], rel_rms(ctl.pol.cpu().numpy(), ref))
+        return a2
+
+    sim.run(step, 80, burn_in=10)
+    r1.close()
+    r2.close()
+    assert worst[0] <= 1e-5, worst[0]
+
+
+def test_pol_predictive_control_runs_and_reports():
+    """The POL evaluation end to end on the tiny system (short training): every law
+    scores the same held-out turbulence and noise, and the switch follows the scores."""
+    from paper_1805_07254_gb300.closed_loop import evaluate_pol
+    res = evaluate_pol(synth.tiny_scao(), train_frames=3000, test_frames=600, steps=300, gains=(0.4, 1.0))
+    print(res)
+    assert set(res["laws"]) == {"integrator_g0.4", "pol_predictor_g0.4", "integrator_g1.0", "pol_predictor_g1.0"}
+    for v in res["laws"].values():
+        assert math.isfinite(v["phase_nm"]) and 0 < v["phase_nm"] < res["open_loop_phase_nm"]
+    assert res["keep_predictor"] == (res["best_pol_predictor"]["phase_nm"] < res["best_integrator"]["phase_nm"])
