@@ -49,6 +49,8 @@ def parse_args(argv=None):
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--store", choices=["f32", "bf16", "f16", "fp8", "int8"], default="f32")
     ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--predictor", action="store_true",
+                    help="the timed controller runs the learned slope predictor (one launch per frame)")
     ap.add_argument("--no-loop", action="store_true")
     # the persistent-loop runs of the serving sizing: 100,000 frames each, paced at 1 kHz
     # and flat out (p99.9 over 1e5 frames rests on 100 samples)
@@ -223,10 +225,11 @@ def make_workload(n_frames, store, cfg=None):
     return cfg, frames.numpy(), dark.numpy(), flat.numpy(), np.ascontiguousarray(M)
 
 
-def workload_config(cfg, store, info=None):
+def workload_config(cfg, store, info=None, predictor=False):
     c = {"workload": f"{cfg.name} ({cfg.frame_side}x{cfg.frame_side} u16 frame, "
                      f"{cfg.n_valid} subaps x {cfg.npx}x{cfg.npx} px, {cfg.nact}x{cfg.nslopes} "
-                     f"{store} control matrix, leaky integrator)",
+                     f"{store} control matrix, {'learned slope predictor, ' if predictor else ''}"
+                     f"leaky integrator)",
          "frame": f"{cfg.frame_side}x{cfg.frame_side}", "n_valid_subaps": cfg.n_valid,
          "nslopes": cfg.nslopes, "nact": cfg.nact, "matrix_store": store,
          "l2": f"flushed between timed steps (read of a {L2_FLUSH_BYTES >> 20} MiB device buffer, outside the events)"}
@@ -375,7 +378,13 @@ def ours(args):
         r.load_cmat(M, store=store)
         return r
 
+    # the predictor's weights do not change the timing
+    from synth.mlp_init import init_mlp_params, flatten
+    pred_params = flatten(init_mlp_params(0))
     r = controller(args.store)
+    if args.predictor:
+        r.load_predictor(pred_params, 0.3)
+        r.set_predictor(True)
     info = r.info()
 
     if world > 1:
@@ -443,8 +452,6 @@ def ours(args):
     # reduced precision + learned predictor: BF16 matrix, predictor on (pixel stage,
     # prediction and streaming reconstruction in one launch); the weights do not
     # change the timing
-    from synth.mlp_init import init_mlp_params, flatten
-    pred_params = flatten(init_mlp_params(0))
     if not args.no_variants:
         rp = controller("bf16")
         rp.load_predictor(pred_params, 0.3)
@@ -553,14 +560,14 @@ def ours(args):
                    "sample": f"{len(times_mt)} ELT frames through the FP64 oracle with {ncores} BLAS "
                              f"threads (time-bounded at {args.cpu_sample_s / 2:.0f} s); p50 per frame"}
 
-    traffic = recorded_traffic(f"elt_{args.store}")
+    traffic = recorded_traffic(f"elt_{args.store}{'_pred' if args.predictor else ''}")
     floor_us = launch_floor(torch, flush, st, min(args.steps, 1000))
     line = {
         "metric": METRIC, "value": round(value, 3), "unit": "us", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": round(s_step["mean"] / 1e3, 6), "higher_is_better": False,
         "scaling": "weak", "vs_baseline": None, "dtype": args.store, "data": "synthetic",
-        "config": workload_config(cfg, args.store, info),
+        "config": workload_config(cfg, args.store, info, args.predictor),
         "p50_us": round(worst["p50"], 3), "p99_us": round(worst["p99"], 3),
         "p999_us": round(worst["p999"], 3), "rms_jitter_us": round(worst["rms_jitter"], 3),
         "peak_to_peak_us": round(worst["peak_to_peak"], 3), "mean_us": round(worst["mean"], 3),

@@ -52,6 +52,13 @@ __device__ unsigned long long g_rtc_stamps[256][8];
     do {                                                               \
         if (tid == 0) g_rtc_stamps[blockIdx.x][i] = rtc_mvm::global_ns(); \
     } while (0)
+// the SM the block runs on, in the last entry
+#define RTC_STAMP_SM()                                                 \
+    do {                                                               \
+        unsigned sm_;                                                  \
+        asm volatile("mov.u32 %0, %%smid;" : "=r"(sm_));               \
+        if (tid == 0) g_rtc_stamps[blockIdx.x][7] = sm_;               \
+    } while (0)
 extern "C" int rtc_probe_stamps(unsigned long long* out, int n) {
     return cudaMemcpyFromSymbol(out, g_rtc_stamps, sizeof(unsigned long long) * 8 * (n < 256 ? n : 256)) ==
                    cudaSuccess
@@ -61,6 +68,9 @@ extern "C" int rtc_probe_stamps(unsigned long long* out, int n) {
 #else
 #define RTC_STAMP(i) \
     do {             \
+    } while (0)
+#define RTC_STAMP_SM() \
+    do {               \
     } while (0)
 #endif
 
@@ -78,8 +88,9 @@ constexpr int kPrefetchTiles = 1;
 constexpr int kPredL2Tiles = RTC_PRED_L2_TILES;
 
 // HOST: the frame is in mapped host memory (rtc_process_frame with pinned buffers):
-// it is read with uncached loads over the host link, and the last block to finish
-// writes the caller's completion record (fh).
+// each block copies its pixel rows into device staging (uncached 16-byte loads over
+// the host link), and the last block to finish writes the caller's completion
+// record (fh).
 template <int DT, int NPX, bool PRED, bool HOST>
 __global__ void __launch_bounds__(kThreads, 1)
 frame_kernel(rtc_pixel::PixelArgs px, Args g, rtc_pred::PredArgs pa, int head,
@@ -88,6 +99,7 @@ frame_kernel(rtc_pixel::PixelArgs px, Args g, rtc_pred::PredArgs pa, int head,
     __shared__ Shared sh;
     const int tid = threadIdx.x;
     RTC_STAMP(0);
+    RTC_STAMP_SM();
     if (tid == 0) init_shared(sh);
     __syncthreads();
     const Plan pl = make_plan(g, smem);
@@ -99,10 +111,6 @@ frame_kernel(rtc_pixel::PixelArgs px, Args g, rtc_pred::PredArgs pa, int head,
     clear_local(g, pl, tid);
     consumer_sync();
 
-    // pixel stage: the block's subapertures, one half-warp each (the ~26
-    // subapertures of a block on the ELT frame take a single round)
-    constexpr int kLoad = HOST ? rtc_pixel::kPixelVolatile : rtc_pixel::kPixelReadOnly;
-    const int slot = 2 * (tid >> 5) + ((tid >> 4) & 1);
     bool gate_open = false;             // every consumer warp arrives exactly once
     auto open_gate = [&gate_open]() {
         if (!gate_open) {
@@ -110,11 +118,26 @@ frame_kernel(rtc_pixel::PixelArgs px, Args g, rtc_pred::PredArgs pa, int head,
             gate_open = true;
         }
     };
+    // a frame in host memory: the block's pixel rows into device staging first, in
+    // 16-byte units over the host link, while the matrix stream already runs (the
+    // host link and HBM do not compete); the pixel stage then reads them through L2
+    if (HOST) {
+        open_gate();
+        rtc_pixel::ingest_block<kConsumers>(px.frame, fh.stage, fh.units, __ldg(fh.blk + blockIdx.x), fh.unit,
+                                            tid);
+        consumer_sync();
+    }
+    const uint16_t* frame = HOST ? fh.stage : px.frame;
+
+    // pixel stage: the block's subapertures, one half-warp each (the ~26
+    // subapertures of a block on the ELT frame take a single round)
+    constexpr int kLoad = HOST ? rtc_pixel::kPixelL2 : rtc_pixel::kPixelReadOnly;
+    const int slot = 2 * (tid >> 5) + ((tid >> 4) & 1);
     for (int base = pl.g0; base < pl.g1; base += 2 * kConsumerWarps) {
         const int gi = base + slot;
         const bool valid = gi < pl.g1;
         const float2 sxy =
-            rtc_pixel::subap_slopes<NPX, kLoad, 16>(px, px.frame, px.s, gi, valid, tid & 31, open_gate);
+            rtc_pixel::subap_slopes<NPX, kLoad, 16>(px, frame, px.s, gi, valid, tid & 31, open_gate);
         if (valid && (tid & 15) == 0) {
             int ix, iy;
             local_index(g, pl, gi, ix, iy);
@@ -217,6 +240,16 @@ cudaError_t launch_dt(rtc_handle* h, const uint16_t* d_frame, float* d_dm_out, f
     if (fhp) {
         fh = *fhp;
         fh.target = h->pf_arrivals + G;
+        // the copy units of each block's pixel rows (16 bytes when the frame allows)
+        const size_t fbytes = static_cast<size_t>(h->cfg.n_wfs) * h->side * h->side * 2;
+        const uintptr_t bases = reinterpret_cast<uintptr_t>(d_frame) | reinterpret_cast<uintptr_t>(h->d_frame);
+        fh.unit = (fbytes % 16 == 0 && bases % 16 == 0) ? 16 : (fbytes % 4 == 0 && bases % 4 == 0) ? 4 : 2;
+        const int rc = build_ingest(h, L.G, fh.unit, 1);
+        if (rc == RTC_ENOMEM) return cudaErrorMemoryAllocation;
+        if (rc != RTC_OK) return cudaErrorUnknown;
+        fh.units = h->d_units;
+        fh.blk = h->d_blk;
+        fh.stage = h->d_frame;
     }
     const cudaError_t e = fhp ? launch_pred<DT, true>(h, L, px, g, pred, head, target, fh, st)
                               : launch_pred<DT, false>(h, L, px, g, pred, head, target, fh, st);

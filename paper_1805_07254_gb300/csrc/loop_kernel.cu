@@ -50,6 +50,9 @@
 namespace {
 
 using namespace rtc_mvm;
+using rtc_pixel::copy_units;
+using rtc_pixel::kNoUnit;
+using rtc_pixel::kUnitRegs;
 
 constexpr unsigned long long kFrameWaitNs = 2000ull * 1000 * 1000;   // 2 s for a frame to arrive
 constexpr unsigned long long kStop = ~0ull;
@@ -78,43 +81,6 @@ struct LoopArgs {
     rtc_pred::PredArgs pa;             // PRED only
     int head0;                         // PRED: ring row of the newest vector at launch
 };
-
-// Units a consumer thread keeps in registers across frames; a block with more
-// than kUnitRegs * kConsumers units reads the rest from the table every frame.
-constexpr int kUnitRegs = 2;
-constexpr unsigned kNoUnit = ~0u;
-
-// The block's copy units of one frame: host slot -> staging, all loads issued
-// before the stores.
-template <typename V>
-__device__ __forceinline__ void copy_units(const uint16_t* frame, uint16_t* stage, const unsigned* units,
-                                           int f1, const unsigned (&ur)[kUnitRegs], int fo) {
-    const V* src = reinterpret_cast<const V*>(frame);
-    V* dst = reinterpret_cast<V*>(stage);
-    V v[kUnitRegs];
-#pragma unroll
-    for (int j = 0; j < kUnitRegs; ++j)
-        if (ur[j] != kNoUnit) v[j] = __ldcv(src + ur[j]);
-    // units beyond the registers, two per thread in flight
-    for (int f = fo; f < f1; f += 2 * kConsumers) {
-        unsigned u[2];
-        V w[2];
-#pragma unroll
-        for (int j = 0; j < 2; ++j) {
-            const int fj = f + j * kConsumers;
-            u[j] = fj < f1 ? __ldg(units + fj) : kNoUnit;
-        }
-#pragma unroll
-        for (int j = 0; j < 2; ++j)
-            if (u[j] != kNoUnit) w[j] = __ldcv(src + u[j]);
-#pragma unroll
-        for (int j = 0; j < 2; ++j)
-            if (u[j] != kNoUnit) __stcg(dst + u[j], w[j]);
-    }
-#pragma unroll
-    for (int j = 0; j < kUnitRegs; ++j)
-        if (ur[j] != kNoUnit) __stcg(dst + ur[j], v[j]);
-}
 
 __device__ __forceinline__ unsigned long long ld_acquire_sys(const unsigned long long* p) {
     unsigned long long v;
@@ -212,11 +178,11 @@ __global__ void __launch_bounds__(kThreads, 1) loop_kernel(LoopArgs L) {
         const uint16_t* frame = L.frames + static_cast<size_t>(slot) * L.frame_elems;
         const int f_over = bk.x + tid + kUnitRegs * kConsumers;
         if (L.copy_unit == 16)
-            copy_units<uint4>(frame, L.stage, L.units, bk.y, ur, f_over);
+            copy_units<uint4, kConsumers>(frame, L.stage, L.units, bk.y, ur, f_over);
         else if (L.copy_unit == 4)
-            copy_units<unsigned>(frame, L.stage, L.units, bk.y, ur, f_over);
+            copy_units<unsigned, kConsumers>(frame, L.stage, L.units, bk.y, ur, f_over);
         else
-            copy_units<unsigned short>(frame, L.stage, L.units, bk.y, ur, f_over);
+            copy_units<unsigned short, kConsumers>(frame, L.stage, L.units, bk.y, ur, f_over);
         consumer_sync();
         const int head = (L.head0 + 1 + static_cast<int>(k & 3)) & 3;
         float* s_k = PRED ? L.pa.ring + static_cast<size_t>(head) * L.kpad
@@ -288,11 +254,15 @@ cudaError_t launch_t(const Launch& Lc, LoopArgs a, cudaStream_t st) {
                                        dim3(Lc.G), dim3(kThreads), args, Lc.smem, st);
 }
 
+}  // namespace
+
 // The copy units and the completing band of every block of a G-block launch
 // (plan_ingest: for each run of the block's subapertures that are neighbours in
 // one row of the subaperture grid, the units its pixel rows cover; sorted and
 // without repeats, so that neighbouring threads read neighbouring units).
 int build_ingest(rtc_handle* h, int G, int unit, int n_bands) {
+    if (h->ingest_G == G && h->ingest_unit == unit && h->ingest_bands == n_bands) return RTC_OK;
+    h->ingest_G = -1;
     std::vector<unsigned> units;
     std::vector<int> b4;
     plan_ingest(h->rc.data(), h->n_valid, h->cfg.npx, h->side, h->sl_g0.data(), h->sl_S, G, unit, n_bands,
@@ -313,8 +283,13 @@ int build_ingest(rtc_handle* h, int G, int unit, int n_bands) {
             cudaSuccess ||
         cudaMemcpy(h->d_blk, blk.data(), G * sizeof(int4), cudaMemcpyHostToDevice) != cudaSuccess)
         return RTC_EDEVICE;
+    h->ingest_G = G;
+    h->ingest_unit = unit;
+    h->ingest_bands = n_bands;
     return RTC_OK;
 }
+
+namespace {
 
 template <int DT>
 cudaError_t launch_dt(rtc_handle* h, const LoopLaunch& ll, cudaStream_t st) {

@@ -152,6 +152,68 @@ __device__ __forceinline__ float2 subap_slopes(const PixelArgs& p, const uint16_
     return res;
 }
 
+// ---- frame ingest from host memory ---------------------------------------------
+// A block copies exactly the pixel rows its subapertures cover from a frame in
+// mapped host memory into a device staging buffer, as a host-built, sorted list of
+// copy units (16 bytes for ELT frames): every load in flight before the stores,
+// bypassing the caches (the host rewrites its buffers between uses).  Two blocks may
+// both copy a unit that straddles their subapertures; they write the same bytes.
+
+// Units a thread keeps in registers (a persistent loop keeps them across frames); a
+// block with more than kUnitRegs * NT units reads the rest from the table.
+constexpr int kUnitRegs = 2;
+constexpr unsigned kNoUnit = ~0u;
+
+// The block's copy units of one frame: host frame -> staging, all loads issued
+// before the stores.  NT threads take part; ur: the thread's first units (kNoUnit
+// for none), fo: its first unit beyond them, f1: the block's end.
+template <typename V, int NT>
+__device__ __forceinline__ void copy_units(const uint16_t* frame, uint16_t* stage, const unsigned* units,
+                                           int f1, const unsigned (&ur)[kUnitRegs], int fo) {
+    const V* src = reinterpret_cast<const V*>(frame);
+    V* dst = reinterpret_cast<V*>(stage);
+    V v[kUnitRegs];
+#pragma unroll
+    for (int j = 0; j < kUnitRegs; ++j)
+        if (ur[j] != kNoUnit) v[j] = __ldcv(src + ur[j]);
+    // units beyond the registers, two per thread in flight
+    for (int f = fo; f < f1; f += 2 * NT) {
+        unsigned u[2];
+        V w[2];
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            const int fj = f + j * NT;
+            u[j] = fj < f1 ? __ldg(units + fj) : kNoUnit;
+        }
+#pragma unroll
+        for (int j = 0; j < 2; ++j)
+            if (u[j] != kNoUnit) w[j] = __ldcv(src + u[j]);
+#pragma unroll
+        for (int j = 0; j < 2; ++j)
+            if (u[j] != kNoUnit) __stcg(dst + u[j], w[j]);
+    }
+#pragma unroll
+    for (int j = 0; j < kUnitRegs; ++j)
+        if (ur[j] != kNoUnit) __stcg(dst + ur[j], v[j]);
+}
+
+// The pixel rows of block `blk` from a host frame into staging (a block's entry of
+// the ingest table: first unit, end unit).  `unit`: bytes per copy unit (16, 4, 2).
+template <int NT>
+__device__ __forceinline__ void ingest_block(const uint16_t* frame, uint16_t* stage, const unsigned* units,
+                                             int4 bk, int unit, int tid) {
+    unsigned ur[kUnitRegs];
+#pragma unroll
+    for (int j = 0; j < kUnitRegs; ++j) {
+        const int f = bk.x + tid + j * NT;
+        ur[j] = f < bk.y ? __ldg(units + f) : kNoUnit;
+    }
+    const int fo = bk.x + tid + kUnitRegs * NT;
+    if (unit == 16) copy_units<uint4, NT>(frame, stage, units, bk.y, ur, fo);
+    else if (unit == 4) copy_units<unsigned, NT>(frame, stage, units, bk.y, ur, fo);
+    else copy_units<unsigned short, NT>(frame, stage, units, bk.y, ur, fo);
+}
+
 }  // namespace rtc_pixel
 
 // Pixel-stage arguments of a handle for one frame (defined in calib_cog.cu).

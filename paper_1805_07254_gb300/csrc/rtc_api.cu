@@ -131,6 +131,7 @@ void cut_slices(rtc_handle* h, const std::vector<int>& g0, int esz, std::vector<
     }
     h->sl_loc[S] = loc;
     h->m_bytes = off;
+    h->ingest_G = -1;                                   // the frame ingest follows the slices
     // 1-byte stores take the plane layout when one lane per row holds (two ring
     // stages of kConsumers rows leave a generous margin of shared memory): their
     // rows then load as 16-byte units (measured: FP8 frame 21.0 against 22.5 us on

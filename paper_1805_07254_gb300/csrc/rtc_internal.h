@@ -43,6 +43,10 @@ struct FrameHost {
     unsigned long long* ctr;     // device count of finished blocks (only grows)
     unsigned long long target;   // the count that completes this launch (set by launch_frame)
     unsigned long long seq;      // value of the record's seq for this call
+    const unsigned* units;       // the blocks' copy units of the frame (build_ingest)
+    const int4* blk;             // [G] first unit, end unit of each block
+    uint16_t* stage;             // device staging of the frame's copied pixels
+    int unit;                    // bytes per copy unit
 };
 
 // Device-visible addresses of the host ring for one rtc_run_loop call.
@@ -113,6 +117,7 @@ struct rtc_handle {
     unsigned* d_units = nullptr;              // frame copy units of each block (see loop_kernel.cu)
     size_t units_cap = 0;                     // entries d_units holds
     int4* d_blk = nullptr;                    // [dev_sms] per block: first unit, end, band, 0
+    int ingest_G = -1, ingest_unit = 0, ingest_bands = 0;   // what d_units / d_blk were built for
     uint16_t* h_ring = nullptr;               // pinned mapped [RTC_LOOP_SLOTS][n_wfs][H][W]
     unsigned long long* h_seq = nullptr;      // pinned mapped [RTC_LOOP_SLOTS]
     float* h_dm_ring = nullptr;               // pinned mapped [RTC_LOOP_SLOTS][nact]
@@ -153,6 +158,10 @@ cudaError_t launch_decay(const rtc_handle* h, float* d_dm_out, cudaStream_t st);
 // Fused frame kernel (pixel stage + grid barrier + streaming MVM + integrator),
 // one cooperative launch per frame; the slopes land in h->d_s.
 cudaError_t frame_kernel_configure();
+
+// The per-block copy units of a frame for a G-block launch (loop_kernel.cu); rebuilt
+// only when G, the unit or the bands change, or the slices were cut again.
+int build_ingest(rtc_handle* h, int G, int unit, int n_bands);
 
 // Persistent loop kernel (see loop_kernel.cu).
 cudaError_t loop_kernel_configure();
