@@ -11,18 +11,20 @@
 // block sum its share of the rows over the slices in a fixed order and apply the
 // integrator (the partial-DM-vector tree of Sec. 2.3.5).
 //
-// The pixel loads are on the frame's critical path: the producer warp waits on a
-// named barrier until every consumer warp has issued its first pixel loads, streams
-// one tile, and holds the rest until the block's slopes are known, so that the pixel
-// loads do not queue behind a flood of bulk copies.
+// The producer warp starts streaming at once: the ring's first tiles are in flight
+// during the launch's cold start (instruction, parameter and table fetches after
+// an L2 flush take the first ~3.5 us before a block can issue its pixel loads), and
+// it holds the rest until the block's slopes are known.  (Measured: waiting for the
+// pixel loads to be issued first, which kept them from queueing behind the bulk
+// copies, came out 0.7-1 us later at the end of the stream.)
 //
 // With the learned slope predictor on (PRED), the measured slopes go into the
 // history ring, a grid barrier makes them visible, each block predicts the next
 // slopes of its own subapertures from their neighbourhoods (pred_tile.cuh, in the
 // shared scratch before the slopes), writing them straight into its local slope
-// vector, and multiplies the prediction.  The producer's hold then lasts through the
-// barrier and the prediction, so it prefetches further tiles into L2 before it
-// waits and the HBM keeps streaming.
+// vector, and multiplies the prediction.  The block arrives at the barrier before it
+// fetches the network's weights (a release would wait for those loads), and the
+// producer's hold lasts through the barrier and the prediction.
 //
 // For rtc_process_frame with pinned host buffers (HOST) the frame is read in place
 // from mapped host memory and the DM commands are written there; the last block to
@@ -38,16 +40,41 @@
 
 #include "mlp.h"
 #include "pixel.cuh"
+
+#ifdef RTC_PHASE_STAMPS
+// Diagnostic build only: %globaltimer at the sub-phases of the fused prediction of
+// each block of the last launch (pred_tile.cuh).
+__device__ unsigned long long g_rtc_pred_stamps[256][8];
+#define RTC_PRED_STAMP(i)                                                          \
+    do {                                                                           \
+        unsigned long long t_;                                                     \
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t_));                     \
+        if (tid == 0) g_rtc_pred_stamps[blockIdx.x][i] = t_;                       \
+    } while (0)
+extern "C" int rtc_probe_pred_stamps(unsigned long long* out, int n) {
+    return cudaMemcpyFromSymbol(out, g_rtc_pred_stamps, sizeof(unsigned long long) * 8 * (n < 256 ? n : 256)) ==
+                   cudaSuccess
+               ? 0
+               : -1;
+}
+#endif
+
 #include "pred_tile.cuh"
 #include "stream_mvm.cuh"
 
 #ifndef RTC_PRED_L2_TILES
-#define RTC_PRED_L2_TILES 4
+#define RTC_PRED_L2_TILES 0
+#endif
+#ifndef RTC_PRED_PREFETCH_TILES
+#define RTC_PRED_PREFETCH_TILES 1
+#endif
+#ifndef RTC_PREFETCH_TILES
+#define RTC_PREFETCH_TILES 2
 #endif
 
 #ifdef RTC_PHASE_STAMPS
 // Diagnostic build only: %globaltimer at the phases of each block of the last launch.
-__device__ unsigned long long g_rtc_stamps[256][8];
+__device__ unsigned long long g_rtc_stamps[256][16];
 #define RTC_STAMP(i)                                                   \
     do {                                                               \
         if (tid == 0) g_rtc_stamps[blockIdx.x][i] = rtc_mvm::global_ns(); \
@@ -60,7 +87,7 @@ __device__ unsigned long long g_rtc_stamps[256][8];
         if (tid == 0) g_rtc_stamps[blockIdx.x][7] = sm_;               \
     } while (0)
 extern "C" int rtc_probe_stamps(unsigned long long* out, int n) {
-    return cudaMemcpyFromSymbol(out, g_rtc_stamps, sizeof(unsigned long long) * 8 * (n < 256 ? n : 256)) ==
+    return cudaMemcpyFromSymbol(out, g_rtc_stamps, sizeof(unsigned long long) * 16 * (n < 256 ? n : 256)) ==
                    cudaSuccess
                ? 0
                : -1;
@@ -78,13 +105,14 @@ namespace {
 
 using namespace rtc_mvm;
 
-// Named barrier on which the producer warp waits until every consumer warp has
-// issued its first pixel loads.
-constexpr int kGateBar = 4;
-// Matrix tiles the producer streams before the block's slopes are known.
-constexpr int kPrefetchTiles = 1;
+// Matrix tiles the producer streams before the block's slopes are known (the
+// ring's two stages).
+constexpr int kPrefetchTiles = RTC_PREFETCH_TILES;
 // With the predictor the hold lasts through the grid barrier and the prediction:
-// this many further tiles stream into L2 meanwhile.
+// this many tiles go to the ring, and this many further ones into L2, meanwhile.
+// (Measured: four L2 tiles made the whole frame 3 us slower than none, their
+// traffic queueing the prediction's latency-bound loads behind it.)
+constexpr int kPredPrefetchTiles = RTC_PRED_PREFETCH_TILES;
 constexpr int kPredL2Tiles = RTC_PRED_L2_TILES;
 
 // HOST: the frame is in mapped host memory (rtc_process_frame with pinned buffers):
@@ -100,29 +128,28 @@ frame_kernel(rtc_pixel::PixelArgs px, Args g, rtc_pred::PredArgs pa, int head,
     const int tid = threadIdx.x;
     RTC_STAMP(0);
     RTC_STAMP_SM();
+    const Plan pl = make_plan(g, smem);
+    // the grid position of a consumer's first subaperture, loaded before the
+    // block's set-up so that its latency overlaps it
+    const int slot = 2 * (tid >> 5) + ((tid >> 4) & 1);
+    const int2 pos0 = rtc_pixel::subap_pos(px, pl.g0 + slot, tid < kConsumers && pl.g0 + slot < pl.g1);
     if (tid == 0) init_shared(sh);
     __syncthreads();
-    const Plan pl = make_plan(g, smem);
+    RTC_STAMP(8);
     if (tid >= kConsumers) {
-        asm volatile("bar.sync %0, %1;" ::"n"(kGateBar), "n"(kThreads) : "memory");
-        if ((tid & 31) == 0) produce(g, pl, sh, 0, true, kPrefetchTiles, PRED ? kPredL2Tiles : 0);
+        if ((tid & 31) == 0)
+            produce(g, pl, sh, 0, true, PRED ? kPredPrefetchTiles : kPrefetchTiles, PRED ? kPredL2Tiles : 0);
         return;
     }
     clear_local(g, pl, tid);
     consumer_sync();
+    RTC_STAMP(9);
 
-    bool gate_open = false;             // every consumer warp arrives exactly once
-    auto open_gate = [&gate_open]() {
-        if (!gate_open) {
-            asm volatile("bar.arrive %0, %1;" ::"n"(kGateBar), "n"(kThreads) : "memory");
-            gate_open = true;
-        }
-    };
+    auto issued = [tid]() { RTC_STAMP(6); };   // the pixel loads are in flight
     // a frame in host memory: the block's pixel rows into device staging first, in
     // 16-byte units over the host link, while the matrix stream already runs (the
     // host link and HBM do not compete); the pixel stage then reads them through L2
     if (HOST) {
-        open_gate();
         rtc_pixel::ingest_block<kConsumers>(px.frame, fh.stage, fh.units, __ldg(fh.blk + blockIdx.x), fh.unit,
                                             tid);
         consumer_sync();
@@ -132,12 +159,12 @@ frame_kernel(rtc_pixel::PixelArgs px, Args g, rtc_pred::PredArgs pa, int head,
     // pixel stage: the block's subapertures, one half-warp each (the ~26
     // subapertures of a block on the ELT frame take a single round)
     constexpr int kLoad = HOST ? rtc_pixel::kPixelL2 : rtc_pixel::kPixelReadOnly;
-    const int slot = 2 * (tid >> 5) + ((tid >> 4) & 1);
     for (int base = pl.g0; base < pl.g1; base += 2 * kConsumerWarps) {
         const int gi = base + slot;
         const bool valid = gi < pl.g1;
+        const int2 pos = base == pl.g0 ? pos0 : rtc_pixel::subap_pos(px, gi, valid);
         const float2 sxy =
-            rtc_pixel::subap_slopes<NPX, kLoad, 16>(px, frame, px.s, gi, valid, tid & 31, open_gate);
+            rtc_pixel::subap_slopes_at<NPX, kLoad, 16>(px, frame, px.s, gi, valid, tid & 31, pos, issued);
         if (valid && (tid & 15) == 0) {
             int ix, iy;
             local_index(g, pl, gi, ix, iy);
@@ -145,7 +172,6 @@ frame_kernel(rtc_pixel::PixelArgs px, Args g, rtc_pred::PredArgs pa, int head,
             pl.loc[iy] = sxy.y;
         }
     }
-    open_gate();                        // a warp without pixel work
     RTC_STAMP(1);
     prefetch_rows<DT>(g, pl, tid);
 
@@ -153,20 +179,30 @@ frame_kernel(rtc_pixel::PixelArgs px, Args g, rtc_pred::PredArgs pa, int head,
     if (PRED) {
         // every block's measured slopes in the history ring, then the prediction of
         // the block's own subapertures, which replaces their local slopes; the
-        // network's registers are fetched while the barrier waits
-        rtc_pred::Regs pr;
-        rtc_pred::prefetch(pa, tid, pl.g0, pl.g1, pr);
+        // network's weights are fetched after the block's arrival, while it waits
         consumer_sync();
-        if (tid == 0) grid_barrier(gridbar, next, g.status, &sh.abort_flag);
+        if (tid == 0) grid_arrive(gridbar);
+        RTC_PRED_STAMP(5);
+        rtc_pred::Regs pr;
+        rtc_pred::prefetch(pa, pl.scratch, tid, pl.g0, pl.g1, head, pr);
+        RTC_PRED_STAMP(6);
+        if (tid == 0) grid_wait(gridbar, next, g.status, &sh.abort_flag);
+        RTC_PRED_STAMP(7);
         consumer_sync();
         next += gridDim.x;
         if (!sh.abort_flag) {
             // the predictions replace the block's local slopes as they are made
-            rtc_pred::predict(pa, pl.scratch, tid, pl.g0, pl.g1, head, pr, [&](int gi, int axis, float v) {
+            auto slot_of = [&](int gi, int axis) {
                 int ix, iy;
                 local_index(g, pl, gi, ix, iy);
-                pl.loc[axis ? iy : ix] = v;
-            });
+                return axis ? iy : ix;
+            };
+            rtc_pred::predict(
+                pa, pl.scratch, tid, pl.g0, pl.g1, head, pr,
+                [&](int gi, int axis) { return pl.loc[slot_of(gi, axis)]; },
+                [&](int gi, int axis, float v) { pl.loc[slot_of(gi, axis)] = v; });
+        } else {
+            rows_landed();              // the prefetch's copies, before the block exits
         }
     }
     consumer_sync();
@@ -174,6 +210,7 @@ frame_kernel(rtc_pixel::PixelArgs px, Args g, rtc_pred::PredArgs pa, int head,
     if (tid == 0) sh.release = 1;       // the rest of the matrix stream may start
     consume<DT>(g, pl, sh, tid, 0);
     RTC_STAMP(3);
+    rows_landed();
 
     // every block's partial vectors before any block sums them
     consumer_sync();

@@ -122,6 +122,7 @@ __global__ void __launch_bounds__(kThreads, 1) loop_kernel(LoopArgs L) {
     // integrator state and row scales of the block's rows: the reduction keeps the
     // shared copy of the state current from frame to frame
     prefetch_rows<DT>(L.mv, pl, tid);
+    rows_landed();                      // once per loop: no need to overlap it
     // the block's calibration data (subaperture-major, contiguous), 128-byte lines
     const int npp = L.px.npx * L.px.npx;
     const long long cal_lines = (static_cast<long long>(pl.g1 - pl.g0) * npp * 4 + 127) / 128;
@@ -203,18 +204,26 @@ __global__ void __launch_bounds__(kThreads, 1) loop_kernel(LoopArgs L) {
         // 3. with the predictor: every block's measured slopes in the history ring,
         //    then the prediction of the block's own subapertures
         if (PRED) {
+            consumer_sync();
+            if (tid == 0) grid_arrive(L.gridbar);
             rtc_pred::Regs pr;
-            rtc_pred::prefetch(L.pa, tid, pl.g0, pl.g1, pr);   // overlaps the barrier's wait
+            rtc_pred::prefetch(L.pa, pl.scratch, tid, pl.g0, pl.g1, head, pr);   // overlaps the barrier's wait
+            if (tid == 0) grid_wait(L.gridbar, G * (kBarriers * k + 1), L.mv.status, &sh.abort_flag);
             consumer_sync();
-            if (tid == 0) grid_barrier(L.gridbar, G * (kBarriers * k + 1), L.mv.status, &sh.abort_flag);
-            consumer_sync();
-            if (sh.abort_flag) break;
+            if (sh.abort_flag) {
+                rows_landed();          // the prefetch's copies, before the block exits
+                break;
+            }
             // the predictions replace the block's local slopes as they are made
-            rtc_pred::predict(L.pa, pl.scratch, tid, pl.g0, pl.g1, head, pr, [&](int gi, int axis, float v) {
+            auto slot_of = [&](int gi, int axis) {
                 int ix, iy;
                 local_index(L.mv, pl, gi, ix, iy);
-                pl.loc[axis ? iy : ix] = v;
-            });
+                return axis ? iy : ix;
+            };
+            rtc_pred::predict(
+                L.pa, pl.scratch, tid, pl.g0, pl.g1, head, pr,
+                [&](int gi, int axis) { return pl.loc[slot_of(gi, axis)]; },
+                [&](int gi, int axis, float v) { pl.loc[slot_of(gi, axis)] = v; });
         }
         consumer_sync();
 

@@ -30,6 +30,7 @@ mvm_stream_kernel(Args g, unsigned long long* gridbar, unsigned long long target
     prefetch_rows<DT>(g, pl, tid);
     consumer_sync();
     consume<DT>(g, pl, sh, tid, 0);
+    rows_landed();
     // every block's partial vectors before any block sums them
     consumer_sync();
     if (tid == 0) grid_barrier(gridbar, target, g.status, &sh.abort_flag);

@@ -84,17 +84,24 @@ struct NoHook {
 // loaded(): called by every lane after each pass has issued its loads (the
 // passes are the same for every lane, valid or not).  Returns (x, y) slopes on the
 // group's first lane (zeros elsewhere).
+//
+// subap_slopes_at takes the subaperture's grid position (subap_pos) from the
+// caller, who may have loaded it early; subap_slopes loads it itself.
+__device__ __forceinline__ int2 subap_pos(const PixelArgs& p, int gi, bool valid) {
+    const int w = valid ? gi / p.n_valid : 0;
+    return valid ? p.rc[gi - w * p.n_valid] : make_int2(0, 0);
+}
+
 template <int NPX, int LD, int L, typename Hook = NoHook>
-__device__ __forceinline__ float2 subap_slopes(const PixelArgs& p, const uint16_t* __restrict__ frame,
-                                             float* __restrict__ s_out, int gi, bool valid, int lane,
-                                             const Hook& loaded = Hook()) {
+__device__ __forceinline__ float2 subap_slopes_at(const PixelArgs& p, const uint16_t* __restrict__ frame,
+                                                float* __restrict__ s_out, int gi, bool valid, int lane,
+                                                int2 pos, const Hook& loaded = Hook()) {
     constexpr int kJ = NPX > 0 ? (NPX * NPX + L - 1) / L : kPixPerLane;
     const int npx = NPX > 0 ? NPX : p.npx;
     const int l = lane & (L - 1);
     const int w = valid ? gi / p.n_valid : 0;
     const int i = valid ? gi - w * p.n_valid : 0;
     const int npp = npx * npx;
-    const int2 pos = valid ? p.rc[i] : make_int2(0, 0);
     const float cc = 0.5f * static_cast<float>(npx - 1);
     const uint16_t* box = frame + static_cast<size_t>(w) * p.side * p.side +
                           static_cast<size_t>(pos.x) * npx * p.side + static_cast<size_t>(pos.y) * npx;
@@ -105,15 +112,23 @@ __device__ __forceinline__ float2 subap_slopes(const PixelArgs& p, const uint16_
     CompSum F{0.f, 0.f}, Sx{0.f, 0.f}, Sy{0.f, 0.f};
     for (int q0 = 0; q0 < npp; q0 += L * kJ) {
         float raw[kJ], dv[kJ], gv[kJ];
+        // the calibration data first: its addresses do not wait for the position
 #pragma unroll
         for (int j = 0; j < kJ; ++j) {
             const int q = q0 + l + L * j;
-            raw[j] = dv[j] = gv[j] = 0.f;
+            dv[j] = gv[j] = 0.f;
+            if (valid && q < npp) {
+                dv[j] = __ldg(dk + q);
+                gv[j] = __ldg(gk + q);
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < kJ; ++j) {
+            const int q = q0 + l + L * j;
+            raw[j] = 0.f;
             if (valid && q < npp) {
                 const int y = q / npx;
                 raw[j] = static_cast<float>(load_pixel<LD>(box + y * p.side + (q - y * npx)));
-                dv[j] = __ldg(dk + q);
-                gv[j] = __ldg(gk + q);
             }
         }
         loaded();
@@ -150,6 +165,13 @@ __device__ __forceinline__ float2 subap_slopes(const PixelArgs& p, const uint16_
         s_w[p.n_valid + i] = res.y;
     }
     return res;
+}
+
+template <int NPX, int LD, int L, typename Hook = NoHook>
+__device__ __forceinline__ float2 subap_slopes(const PixelArgs& p, const uint16_t* __restrict__ frame,
+                                             float* __restrict__ s_out, int gi, bool valid, int lane,
+                                             const Hook& loaded = Hook()) {
+    return subap_slopes_at<NPX, LD, L>(p, frame, s_out, gi, valid, lane, subap_pos(p, gi, valid), loaded);
 }
 
 // ---- frame ingest from host memory ---------------------------------------------

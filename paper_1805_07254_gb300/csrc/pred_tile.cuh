@@ -21,6 +21,12 @@
 
 #include "stream_mvm.cuh"
 
+#ifndef RTC_PRED_STAMP
+#define RTC_PRED_STAMP(i) \
+    do {                  \
+    } while (0)
+#endif
+
 namespace rtc_pred {
 
 using rtc_mvm::consumer_sync;
@@ -49,10 +55,12 @@ constexpr int OFF_B3 = OFF_W3 + NO * NH;
 constexpr int SM_X = 0;                              // bf16 [TS][XP]
 constexpr int SM_H1 = SM_X + TS * XP * 2;            // bf16 [TS][HP]
 constexpr int SM_H2 = SM_H1 + TS * HP * 2;           // f32 [TS][H2P]
-constexpr int kSmemBytes = SM_H2 + TS * H2P * 4;
+constexpr int SM_W3 = SM_H2 + TS * H2P * 4;          // f32 W3 [NO][NH], then b3 [NO]
+constexpr int kSmemBytes = SM_W3 + (NO * NH + NO + 2) * 4;
 
 static_assert(kPairRounds == 2, "gather registers assume two rounds of pairs");
-static_assert(SM_H1 % 16 == 0 && SM_H2 % 16 == 0, "alignment");
+static_assert(SM_H1 % 16 == 0 && SM_H2 % 16 == 0 && SM_W3 % 16 == 0, "alignment");
+static_assert(OFF_B3 == OFF_W3 + NO * NH, "W3 and b3 are one run of the parameters");
 static_assert(NF % 8 == 0 && NF + 8 == KP, "the last k step holds 8 features and 8 zero columns");
 
 struct PredArgs {
@@ -91,6 +99,7 @@ struct Regs {
     uint32_t w2f[NH / 16][2];   // B fragments of W2
     float b1v[2], b2v[2];       // biases of the thread's two accumulator columns
     int jn[kPairRounds];        // neighbour indices of the first tile's pairs
+    float vo[kPairRounds][6];   // their slopes of the three older frames (lags 1-3)
 };
 
 // Neighbour index of pair p (sample p / 25, neighbour p % 25) of the tile at t0.
@@ -100,9 +109,18 @@ __device__ __forceinline__ int pair_nbr(const PredArgs& pa, int t0, int i1, int 
     return i < i1 ? __ldg(pa.nbr + static_cast<size_t>(i) * 25 + (p - (p / 25) * 25)) : -1;
 }
 
-// The thread's registers that do not depend on the frame.  [i0, i1): the block's
-// subapertures.
-__device__ __forceinline__ void prefetch(const PredArgs& pa, int tid, int i0, int i1, Regs& r) {
+// What the first tile needs that does not depend on this frame's slopes: the
+// weight fragments, biases and neighbour indices in registers, the first tile's
+// features of the three older frames (ring rows head-1 .. head-3, written by earlier
+// frames) in registers, and the output layer's weights in the scratch sm
+// (asynchronous copies, complete once predict's first barrier has passed).
+// [i0, i1): the block's subapertures.  Call it after the block's grid-barrier
+// arrival (a release would wait for these loads) and before its wait.
+__device__ __forceinline__ void prefetch(const PredArgs& pa, unsigned char* sm, int tid, int i0, int i1,
+                                         int head, Regs& r) {
+    float* w3s = reinterpret_cast<float*>(sm + SM_W3);
+    for (int k = tid; k < NO * NH + NO; k += kConsumers) rtc_mvm::cp_async4(w3s + k, pa.params + OFF_W3 + k);
+    asm volatile("cp.async.commit_group;" ::: "memory");
     const int warp = tid >> 5, lane = tid & 31;
     const int g = lane >> 2, t = lane & 3;
     if (warp < kMmaWarps) {
@@ -126,47 +144,55 @@ __device__ __forceinline__ void prefetch(const PredArgs& pa, int tid, int i0, in
     }
 #pragma unroll
     for (int q = 0; q < kPairRounds; ++q) r.jn[q] = pair_nbr(pa, i0, i1, tid + q * kConsumers);
+#pragma unroll
+    for (int q = 0; q < kPairRounds; ++q)
+#pragma unroll
+        for (int la = 2; la < 8; ++la) {
+            const float* row = pa.ring + static_cast<size_t>((head - (la >> 1)) & 3) * pa.kpad;
+            r.vo[q][la - 2] = r.jn[q] >= 0 ? __ldcg(row + (la & 1) * pa.nv + r.jn[q]) : 0.f;
+        }
 }
-
-struct NoSink {
-    __device__ void operator()(int, int, float) const {}
-};
 
 // After the grid barrier that completes the measured slopes: predictions of
 // subapertures [i0, i1) from the ring rows head, head-1, head-2, head-3 (newest
-// first), with the registers `prefetch` filled (before the barrier, so that the
-// weight and neighbour loads overlap the wait).  Every consumer thread calls it;
-// sm is TS-sample scratch of kSmemBytes.  Each prediction goes to pa.s_pred and to
-// sink(i, axis, value).  Ends with a consumer barrier.
-template <typename Sink = NoSink>
+// first), with the registers and scratch `prefetch` filled (before the barrier, so
+// that the weight and neighbour loads overlap the wait).  Every consumer thread
+// calls it; sm is TS-sample scratch of kSmemBytes.  src(i, axis) gives the block's
+// own copy of the measured slope s_k of subaperture i (the value in ring row head);
+// each prediction goes to pa.s_pred and to sink(i, axis, value), after the same
+// thread's src read of that slope.  Ends with a consumer barrier.
+template <typename Src, typename Sink>
 __device__ __forceinline__ void predict(const PredArgs& pa, unsigned char* sm, int tid, int i0, int i1,
-                                        int head, const Regs& r, const Sink& sink = Sink()) {
+                                        int head, const Regs& r, const Src& src, const Sink& sink) {
     const int warp = tid >> 5, lane = tid & 31;
     const int g = lane >> 2, t = lane & 3;
     __nv_bfloat16* X = reinterpret_cast<__nv_bfloat16*>(sm + SM_X);
     __nv_bfloat16* H1 = reinterpret_cast<__nv_bfloat16*>(sm + SM_H1);
     float* H2 = reinterpret_cast<float*>(sm + SM_H2);
-    const float* W3 = pa.params + OFF_W3;
-    const float* b3 = pa.params + OFF_B3;
+    const float* W3 = reinterpret_cast<const float*>(sm + SM_W3);
+    const float* b3 = W3 + NO * NH;
     const float* rows[4];
 #pragma unroll
     for (int lag = 0; lag < 4; ++lag)
         rows[lag] = pa.ring + static_cast<size_t>((head - lag) & 3) * pa.kpad;
 
+    RTC_PRED_STAMP(0);
     for (int t0 = i0; t0 < i1; t0 += TS) {
         int jn[kPairRounds];
 #pragma unroll
         for (int q = 0; q < kPairRounds; ++q)
             jn[q] = t0 == i0 ? r.jn[q] : pair_nbr(pa, t0, i1, tid + q * kConsumers);
         // gather: every load of the thread's pairs in flight before any store; the
-        // rows were written by other blocks of this kernel, so read them from L2
+        // newest row was written by other blocks of this kernel, so it is read from
+        // L2 (the first tile's older rows came with prefetch)
         float v[kPairRounds][8];
 #pragma unroll
         for (int q = 0; q < kPairRounds; ++q)
 #pragma unroll
             for (int la = 0; la < 8; ++la) {
                 const int j = jn[q];
-                v[q][la] = j >= 0 ? __ldcg(rows[la >> 1] + (la & 1) * pa.nv + j) : 0.f;
+                if (la >= 2 && t0 == i0) v[q][la] = r.vo[q][la - 2];
+                else v[q][la] = j >= 0 ? __ldcg(rows[la >> 1] + (la & 1) * pa.nv + j) : 0.f;
             }
 #pragma unroll
         for (int q = 0; q < kPairRounds; ++q) {
@@ -178,7 +204,9 @@ __device__ __forceinline__ void predict(const PredArgs& pa, unsigned char* sm, i
                     X[s * XP + la * 25 + nb] = __float2bfloat16_rn(v[q][la] * pa.inv_sigma);
             }
         }
+        if (t0 == i0) rtc_mvm::rows_landed();     // the output layer's weights (prefetch)
         consumer_sync();
+        RTC_PRED_STAMP(1);
 
         // hidden layer 1: z1 = X W1^T + b1, h1 = GELU(z1) as BF16; the upper half of
         // the last k step is the zero padding of W1 and X (not stored: zero fragments)
@@ -204,6 +232,7 @@ __device__ __forceinline__ void predict(const PredArgs& pa, unsigned char* sm, i
                 }
         }
         consumer_sync();
+        RTC_PRED_STAMP(2);
 
         // hidden layer 2: z2 = h1 W2^T + b2, h2 = GELU(z2) in FP32
         if (warp < kMmaWarps) {
@@ -226,23 +255,25 @@ __device__ __forceinline__ void predict(const PredArgs& pa, unsigned char* sm, i
                 }
         }
         consumer_sync();
+        RTC_PRED_STAMP(3);
 
         // output layer on CUDA cores and the predicted next slopes
         if (tid < TS * NO) {
             const int s = tid >> 1, o = tid & 1;
             const int i = t0 + s;
             if (i < i1) {
-                float y = __ldg(b3 + o);
+                float y = b3[o];
 #pragma unroll 16
-                for (int j = 0; j < NH; ++j) y = fmaf(H2[s * H2P + j], __ldg(W3 + o * NH + j), y);
-                const int idx = o * pa.nv + i;
-                const float sp = __fmaf_rn(pa.sigma, y, __ldcg(rows[0] + idx));
-                pa.s_pred[idx] = sp;
+                for (int j = 0; j < NH; ++j) y = fmaf(H2[s * H2P + j], W3[o * NH + j], y);
+                const float sp = __fmaf_rn(pa.sigma, y, src(i, o));
+                pa.s_pred[o * pa.nv + i] = sp;
                 sink(i, o, sp);
             }
         }
         consumer_sync();
+        RTC_PRED_STAMP(4);
     }
+    if (i0 >= i1) rtc_mvm::rows_landed();         // no tile: still no copy left in flight
 }
 
 }  // namespace rtc_pred

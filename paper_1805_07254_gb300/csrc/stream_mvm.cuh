@@ -392,14 +392,29 @@ __device__ __forceinline__ void gather_local(const Args& g, const Plan& pl, int 
     }
 }
 
-// Consumers: integrator state and row scales of the rows the block reduces.
+// 4-byte global -> shared copy that does not hold up the issuing thread.
+__device__ __forceinline__ void cp_async4(void* dst, const void* src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+}
+
+// Consumers: integrator state and row scales of the rows the block reduces, as
+// asynchronous copies, so that the block's first tiles need not wait for them (a
+// cold load here held every frame's stream back by about a round trip).  The
+// copies are complete once rows_landed() and a consumer barrier have followed.
 template <int DT>
 __device__ __forceinline__ void prefetch_rows(const Args& g, const Plan& pl, int tid) {
     for (int r = pl.r0 + tid; r < pl.r1; r += kConsumers) {
-        pl.a_pre[r - pl.r0] = __ldcg(g.a + r);
-        pl.sc_pre[r - pl.r0] = RowScaled<DT>::v ? g.scale[r] : 1.f;
+        cp_async4(pl.a_pre + (r - pl.r0), g.a + r);
+        if (RowScaled<DT>::v) cp_async4(pl.sc_pre + (r - pl.r0), g.scale + r);
+        else pl.sc_pre[r - pl.r0] = 1.f;
     }
+    asm volatile("cp.async.commit_group;" ::: "memory");
 }
+
+// The calling thread's prefetch_rows copies have landed.  Every consumer calls it
+// before the barrier that precedes reduce_rows, aborted or not (no copy may still
+// be writing shared memory when the block exits).
+__device__ __forceinline__ void rows_landed() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 // Rows of slice tiles with rb bytes per row: R rows for the widest slice, a multiple
 // of R that still fits in a stage for narrower ones.  A row is always summed by
@@ -780,9 +795,16 @@ __device__ __forceinline__ void reduce_rows(const Args& g, const Plan& pl, int t
 // every block after its second one (no separate fences).  The counter only grows;
 // the caller passes the arrival count that completes this barrier.  False (and
 // RTC_ETIMEDOUT in the status word) if it did not complete within kWaitNs.
-__device__ __forceinline__ bool grid_barrier(unsigned long long* bar, unsigned long long target,
-                                             int* status, volatile int* abort) {
+//
+// The two halves may also be called apart (grid_arrive, then grid_wait): loads the
+// thread issues in between do not hold up its arrival, which a release would
+// otherwise wait for.
+__device__ __forceinline__ void grid_arrive(unsigned long long* bar) {
     asm volatile("red.release.gpu.global.add.u64 [%0], 1;" ::"l"(bar) : "memory");
+}
+
+__device__ __forceinline__ bool grid_wait(unsigned long long* bar, unsigned long long target, int* status,
+                                          volatile int* abort) {
     const unsigned long long t0 = global_ns();
     while (true) {
         unsigned long long v;
@@ -795,6 +817,12 @@ __device__ __forceinline__ bool grid_barrier(unsigned long long* bar, unsigned l
         }
     }
     return true;
+}
+
+__device__ __forceinline__ bool grid_barrier(unsigned long long* bar, unsigned long long target,
+                                             int* status, volatile int* abort) {
+    grid_arrive(bar);
+    return grid_wait(bar, target, status, abort);
 }
 
 // Grid, tiles, stages and dynamic shared memory of a launch for one handle.
