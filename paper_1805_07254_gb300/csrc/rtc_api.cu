@@ -296,6 +296,18 @@ void* mapped_view(void* p) { return const_cast<void*>(mapped_view(static_cast<co
 
 constexpr double kHostWaitS = 2.0;      // bound on the host's wait for a frame's record
 
+#ifdef RTC_HOST_STAMPS
+// Diagnostic build only: steady-clock times (ns) of the last rtc_process_frame call
+// with pinned buffers: entry, buffers resolved, launch enqueued, record seen, return.
+long long g_host_stamps[5];
+#define RTC_HOST_STAMP(i) \
+    g_host_stamps[i] = std::chrono::duration_cast<std::chrono::nanoseconds>(std::chrono::steady_clock::now().time_since_epoch()).count()
+#else
+#define RTC_HOST_STAMP(i) \
+    do {                  \
+    } while (0)
+#endif
+
 // rtc_process_frame on pinned host buffers: one launch reads the frame over the host
 // link and writes the DM commands there; the host waits for the completion record.
 int process_mapped(rtc_handle* h, const uint16_t* d_frame_host, float* d_dm_host, float* slopes_out) {
@@ -313,6 +325,7 @@ int process_mapped(rtc_handle* h, const uint16_t* d_frame_host, float* d_dm_host
     const float* s_used = nullptr;
     const int rc = enqueue_step(h, d_frame_host, d_dm_host, nullptr, h->stream, &s_used, &fh);
     if (rc != RTC_OK) return rc;
+    RTC_HOST_STAMP(2);
     const auto t0 = std::chrono::steady_clock::now();
     while (__atomic_load_n(&h->h_pf_done->seq, __ATOMIC_ACQUIRE) != fh.seq) {
         if (std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count() > kHostWaitS) {
@@ -322,6 +335,7 @@ int process_mapped(rtc_handle* h, const uint16_t* d_frame_host, float* d_dm_host
             return fail(h, RTC_ETIMEDOUT, "the frame's completion record did not arrive");
         }
     }
+    RTC_HOST_STAMP(3);
     if (__atomic_load_n(&h->h_pf_done->status, __ATOMIC_RELAXED) != RTC_OK) return take_status(h, h->stream);
     if (slopes_out) {
         RTC_CUDA(h, cudaMemcpyAsync(slopes_out, s_used, h->nslopes * sizeof(float), cudaMemcpyDeviceToHost,
@@ -745,6 +759,7 @@ int rtc_get_info(const rtc_handle* h, rtc_info* out) {
 }
 
 int rtc_process_frame(rtc_handle* h, const uint16_t* frame, float* dm_out, float* slopes_out) {
+    RTC_HOST_STAMP(0);
     int rc = check_ready(h);
     if (rc != RTC_OK) return rc;
     if (h->in_slot.load()) return fail(h, RTC_ESTATE, "the handle's job is in a server slot");
@@ -754,7 +769,12 @@ int rtc_process_frame(rtc_handle* h, const uint16_t* frame, float* dm_out, float
     // the commands over the host link, no copies and no stream synchronisation
     const uint16_t* d_frame_host = static_cast<const uint16_t*>(mapped_view(frame));
     float* d_dm_host = static_cast<float*>(mapped_view(dm_out));
-    if (d_frame_host && d_dm_host && h->kpad > 0) return process_mapped(h, d_frame_host, d_dm_host, slopes_out);
+    RTC_HOST_STAMP(1);
+    if (d_frame_host && d_dm_host && h->kpad > 0) {
+        rc = process_mapped(h, d_frame_host, d_dm_host, slopes_out);
+        RTC_HOST_STAMP(4);
+        return rc;
+    }
     const size_t fbytes = static_cast<size_t>(h->cfg.n_wfs) * h->side * h->side * sizeof(uint16_t);
     RTC_CUDA(h, cudaMemcpyAsync(h->d_frame, frame, fbytes, cudaMemcpyHostToDevice, h->stream));
     const float* s_used = nullptr;
@@ -837,3 +857,9 @@ int rtc_synchronize(rtc_handle* h, void* stream) {
 }
 
 }  // extern "C"
+
+#ifdef RTC_HOST_STAMPS
+extern "C" void rtc_probe_host_stamps(long long* out) {
+    for (int i = 0; i < 5; ++i) out[i] = g_host_stamps[i];
+}
+#endif
