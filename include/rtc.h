@@ -313,6 +313,34 @@ typedef struct rtc_stats {
  * RTC_EDEVICE, RTC_ETIMEDOUT. */
 int rtc_run_loop(rtc_handle* h, const rtc_loop_config* cfg, rtc_stats* stats);
 
+/* ---- resident per-frame calls --------------------------------------------------
+ * The same persistent kernel, driven one frame at a time by the caller's own
+ * thread (a camera callback, say) instead of by a frame source: after
+ * rtc_resident_start, each rtc_process_frame call on pinned (page-locked, mapped)
+ * buffers publishes the frame and waits for its DM commands, with no kernel launch
+ * per frame (the paper's continuously running RTC threads, Sec. 2.3.2).  The
+ * kernel reads the frame from the caller's buffer and writes the commands into
+ * the caller's dm_out; both must stay valid until the call returns, the frame
+ * buffer must be 16-byte aligned and dm_out 4-byte aligned.  Results are those of
+ * the per-frame launches bit for bit, the integrator (and predictor history) carry
+ * over in both directions, and the learned predictor runs if it is on.
+ *
+ * While resident the kernel occupies every SM of the handle's device, spinning on
+ * the next frame's flag.  If no frame comes for 2 s its bounded wait expires and
+ * it exits; the next rtc_process_frame relaunches it transparently.  Other calls
+ * on the handle that touch the device (loading maps or a matrix, the stage and
+ * async calls, rtc_run_loop, a server slot, rtc_process_frame with pageable
+ * buffers or slopes_out) return RTC_ESTATE until rtc_resident_stop; device
+ * memory releases of any handle are queued until then (as during rtc_run_loop).
+ * rtc_destroy stops a resident handle first.
+ * Errors: RTC_EINVAL, RTC_ESTATE (not ready, in a server slot, already resident),
+ * RTC_ENOMEM, RTC_EDEVICE. */
+int rtc_resident_start(rtc_handle* h);
+
+/* Stop the resident kernel (no-op if the handle is not resident).  Errors:
+ * RTC_EINVAL, RTC_EDEVICE, RTC_ETIMEDOUT (a grid barrier of the kernel expired). */
+int rtc_resident_stop(rtc_handle* h);
+
 /* ---- serving several loops on one GPU (continuous batching) --------------------
  * A server runs independent controllers (handles, each with its own calibration,
  * matrix, integrator and predictor history) side by side on one device.  A job

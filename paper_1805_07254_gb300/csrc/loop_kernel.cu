@@ -47,6 +47,25 @@
 #include "pred_tile.cuh"
 #include "stream_mvm.cuh"
 
+#ifdef RTC_PHASE_STAMPS
+// Diagnostic build only: %globaltimer at the phases of each block's last frame.
+__device__ unsigned long long g_rtc_loop_stamps[256][8];
+#define RTC_LOOP_STAMP(i)                                                        \
+    do {                                                                         \
+        if (tid == 0) g_rtc_loop_stamps[blockIdx.x][i] = rtc_mvm::global_ns();   \
+    } while (0)
+extern "C" int rtc_probe_loop_stamps(unsigned long long* out, int n) {
+    return cudaMemcpyFromSymbol(out, g_rtc_loop_stamps, sizeof(unsigned long long) * 8 * (n < 256 ? n : 256)) ==
+                   cudaSuccess
+               ? 0
+               : -1;
+}
+#else
+#define RTC_LOOP_STAMP(i) \
+    do {                  \
+    } while (0)
+#endif
+
 namespace {
 
 using namespace rtc_mvm;
@@ -68,6 +87,8 @@ struct LoopArgs {
     const int4* blk;                   // [G] first unit, end unit, band that completes the block
     int n_bands;                       // bands per frame: frame k band j is k * n_bands + j + 1
     const unsigned long long* seq;     // mapped host [nslot]: bands published
+    const unsigned long long* ptrs;    // mapped host [nslot][2] or null: the frame's own
+                                       // frame and DM buffers (device views; resident mode)
     float* dm_ring;                    // mapped host [nslot][nact]
     rtc_loop_done* done;               // mapped host [nslot]
     float* s_buf;                      // device [2][kpad]
@@ -87,6 +108,11 @@ __device__ __forceinline__ unsigned long long ld_acquire_sys(const unsigned long
     asm volatile("ld.acquire.sys.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
     return v;
 }
+__device__ __forceinline__ unsigned long long ld_relaxed_sys(const unsigned long long* p) {
+    unsigned long long v;
+    asm volatile("ld.relaxed.sys.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
 __device__ __forceinline__ void st_release_sys(unsigned long long* p, unsigned long long v) {
     asm volatile("st.release.sys.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
@@ -96,6 +122,8 @@ __global__ void __launch_bounds__(kThreads, 1) loop_kernel(LoopArgs L) {
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ Shared sh;
     __shared__ int stop_now;
+    __shared__ const uint16_t* frame_in;     // this frame's pixels (ring slot or caller's buffer)
+    __shared__ float* dm_to;                 // where this frame's DM commands go
     const int tid = threadIdx.x;
     const unsigned long long G = gridDim.x;
     // the block's plan lives in shared memory: kept in registers across the frame
@@ -170,13 +198,21 @@ __global__ void __launch_bounds__(kThreads, 1) loop_kernel(LoopArgs L) {
             if (!stop) atomicMax(L.t_seen + (k & 1), t);
             if (stop) sh.abort_flag = 1;            // the producer stops too
             stop_now = stop;
+            // the frame's buffers: written by the host before it published the frame
+            frame_in = L.frames + static_cast<size_t>(slot) * L.frame_elems;
+            dm_to = L.dm_ring + static_cast<size_t>(slot) * L.mv.nact;
+            if (L.ptrs && !stop) {
+                frame_in = reinterpret_cast<const uint16_t*>(ld_relaxed_sys(L.ptrs + 2 * slot));
+                dm_to = reinterpret_cast<float*>(ld_relaxed_sys(L.ptrs + 2 * slot + 1));
+            }
         }
         consumer_sync();
         if (stop_now) break;
+        RTC_LOOP_STAMP(0);
 
         // 2. the block's pixels into device memory, then the block's slopes from
         //    them, into the local vector (and the global one)
-        const uint16_t* frame = L.frames + static_cast<size_t>(slot) * L.frame_elems;
+        const uint16_t* frame = frame_in;
         const int f_over = bk.x + tid + kUnitRegs * kConsumers;
         if (L.copy_unit == 16)
             copy_units<uint4, kConsumers>(frame, L.stage, L.units, bk.y, ur, f_over);
@@ -185,6 +221,7 @@ __global__ void __launch_bounds__(kThreads, 1) loop_kernel(LoopArgs L) {
         else
             copy_units<unsigned short, kConsumers>(frame, L.stage, L.units, bk.y, ur, f_over);
         consumer_sync();
+        RTC_LOOP_STAMP(1);
         const int head = (L.head0 + 1 + static_cast<int>(k & 3)) & 3;
         float* s_k = PRED ? L.pa.ring + static_cast<size_t>(head) * L.kpad
                           : L.s_buf + static_cast<size_t>(k & 1) * L.kpad;
@@ -231,12 +268,16 @@ __global__ void __launch_bounds__(kThreads, 1) loop_kernel(LoopArgs L) {
         //    and integrated; DM commands to the device state and the frame's host slot
         Args mv = L.mv;
         mv.partial = L.mv.partial + (k & 1) * L.partial_stride;
+        RTC_LOOP_STAMP(2);
         tile = consume<DT>(mv, pl, sh, tid, tile);
+        RTC_LOOP_STAMP(3);
         consumer_sync();
         if (tid == 0) grid_barrier(L.gridbar, G * (kBarriers * k + kBarriers), L.mv.status, &sh.abort_flag);
         consumer_sync();
         if (sh.abort_flag) break;
-        reduce_rows<DT>(mv, pl, tid, L.dm_ring + static_cast<size_t>(slot) * L.mv.nact);
+        RTC_LOOP_STAMP(4);
+        reduce_rows<DT>(mv, pl, tid, dm_to);
+        RTC_LOOP_STAMP(5);
 
         // 5. the last block to finish publishes the completion record
         consumer_sync();
@@ -322,6 +363,7 @@ cudaError_t launch_dt(rtc_handle* h, const LoopLaunch& ll, cudaStream_t st) {
     a.blk = h->d_blk;
     a.n_bands = ll.n_bands;
     a.seq = ll.d_seq;
+    a.ptrs = ll.d_ptrs;
     a.dm_ring = ll.d_dm;
     a.done = ll.d_done;
     a.s_buf = h->d_sbuf;

@@ -233,6 +233,12 @@ int apply_subaps(rtc_handle* h, const std::vector<int32_t>& rc) {
 
 int fail_handle(rtc_handle* h, int code, const char* msg) { return fail(h, code, "%s", msg); }
 
+int handle_busy(rtc_handle* h) {
+    if (h->in_slot.load()) return fail(h, RTC_ESTATE, "the handle's job is in a server slot");
+    if (h->resident) return fail(h, RTC_ESTATE, "the handle is resident (rtc_resident_stop first)");
+    return RTC_OK;
+}
+
 // Read (and clear) the device status word after the stream has drained.
 
 int take_status(rtc_handle* h, cudaStream_t st) {
@@ -448,6 +454,10 @@ int rtc_create(const rtc_config* cfg, rtc_handle** out) {
 int rtc_destroy(rtc_handle* h) {
     if (!h) return RTC_OK;
     if (h->in_slot.load()) return fail(h, RTC_ESTATE, "the handle's job is in a server slot");
+    if (h->resident) {
+        DeviceScope ds(h->cfg.device);
+        resident_stop(h);
+    }
     if (release_or_defer([h] { rtc_destroy(h); })) return RTC_OK;
     DeviceScope ds(h->cfg.device);
     if (h->stream) cudaStreamSynchronize(h->stream);
@@ -475,6 +485,7 @@ int rtc_destroy(rtc_handle* h) {
     if (h->h_seq) cudaFreeHost(h->h_seq);
     if (h->h_dm_ring) cudaFreeHost(h->h_dm_ring);
     if (h->h_done) cudaFreeHost(h->h_done);
+    if (h->h_ptrs) cudaFreeHost(h->h_ptrs);
     if (h->h_status) cudaFreeHost(h->h_status);
     h->h_status = nullptr;
     if (h->stream) cudaStreamDestroy(h->stream);
@@ -484,7 +495,7 @@ int rtc_destroy(rtc_handle* h) {
 
 int rtc_load_subaps(rtc_handle* h, const int32_t* rc, int32_t n_valid) {
     if (!h) return RTC_EINVAL;
-    if (h->in_slot.load()) return fail(h, RTC_ESTATE, "the handle's job is in a server slot");
+    if (const int busy = handle_busy(h)) return busy;
     if (n_valid < 0 || (n_valid > 0 && !rc)) return fail(h, RTC_EINVAL, "bad subap map");
     DeviceScope ds(h->cfg.device);
     RTC_CUDA(h, cudaStreamSynchronize(h->stream));
@@ -494,7 +505,7 @@ int rtc_load_subaps(rtc_handle* h, const int32_t* rc, int32_t n_valid) {
 
 int rtc_load_calib(rtc_handle* h, const float* dark, const float* flat, int64_t npix) {
     if (!h) return RTC_EINVAL;
-    if (h->in_slot.load()) return fail(h, RTC_ESTATE, "the handle's job is in a server slot");
+    if (const int busy = handle_busy(h)) return busy;
     const int side = h->side, npx = h->cfg.npx, nw = h->cfg.n_wfs, nv = h->n_valid;
     const int64_t want = static_cast<int64_t>(nw) * side * side;
     if (!dark || !flat || npix != want)
@@ -533,7 +544,7 @@ int rtc_load_calib(rtc_handle* h, const float* dark, const float* flat, int64_t 
 
 int rtc_set_threshold(rtc_handle* h, int32_t mode, float thr) {
     if (!h) return RTC_EINVAL;
-    if (h->in_slot.load()) return fail(h, RTC_ESTATE, "the handle's job is in a server slot");
+    if (const int busy = handle_busy(h)) return busy;
     if ((mode != 0 && mode != 1) || !isfinite(thr)) return fail(h, RTC_EINVAL, "bad threshold");
     h->thr_mode = mode;
     h->thr = thr;
@@ -543,7 +554,7 @@ int rtc_set_threshold(rtc_handle* h, int32_t mode, float thr) {
 int rtc_load_cmat(rtc_handle* h, const void* M, int32_t nact, int32_t nslopes, int32_t src,
                   int32_t store, const float* row_scales) {
     if (!h) return RTC_EINVAL;
-    if (h->in_slot.load()) return fail(h, RTC_ESTATE, "the handle's job is in a server slot");
+    if (const int busy = handle_busy(h)) return busy;
     if (!M) return fail(h, RTC_EINVAL, "M is NULL");
     if (nact != h->cfg.nact || nslopes != h->nslopes)
         return fail(h, RTC_EINVAL, "matrix is %dx%d, handle expects %dx%d", nact, nslopes, h->cfg.nact, h->nslopes);
@@ -601,7 +612,7 @@ int rtc_load_cmat(rtc_handle* h, const void* M, int32_t nact, int32_t nslopes, i
 
 int rtc_set_readout(rtc_handle* h, int32_t n_bands, double band_interval_us) {
     if (!h) return RTC_EINVAL;
-    if (h->in_slot.load()) return fail(h, RTC_ESTATE, "the handle's job is in a server slot");
+    if (const int busy = handle_busy(h)) return busy;
     if (n_bands < 0 || n_bands > h->side || !(band_interval_us >= 0.0) || !(band_interval_us <= 1e6))
         return fail(h, RTC_EINVAL, "n_bands must be 0 .. frame height and band_interval_us in [0, 1e6]");
     DeviceScope ds(h->cfg.device);
@@ -658,7 +669,7 @@ int rtc_set_readout(rtc_handle* h, int32_t n_bands, double band_interval_us) {
 
 int rtc_set_gain(rtc_handle* h, float gain, float leak) {
     if (!h) return RTC_EINVAL;
-    if (h->in_slot.load()) return fail(h, RTC_ESTATE, "the handle's job is in a server slot");
+    if (const int busy = handle_busy(h)) return busy;
     if (!isfinite(gain) || !isfinite(leak)) return fail(h, RTC_EINVAL, "gain and leak must be finite");
     h->gain = gain;
     h->leak = leak;
@@ -667,7 +678,7 @@ int rtc_set_gain(rtc_handle* h, float gain, float leak) {
 
 int rtc_reset(rtc_handle* h) {
     if (!h) return RTC_EINVAL;
-    if (h->in_slot.load()) return fail(h, RTC_ESTATE, "the handle's job is in a server slot");
+    if (const int busy = handle_busy(h)) return busy;
     DeviceScope ds(h->cfg.device);
     RTC_CUDA(h, cudaMemsetAsync(h->d_a, 0, h->cfg.nact * sizeof(float), h->stream));
     if (h->d_ring)
@@ -679,7 +690,7 @@ int rtc_reset(rtc_handle* h) {
 
 int rtc_load_predictor(rtc_handle* h, const float* params, int64_t n, float sigma) {
     if (!h) return RTC_EINVAL;
-    if (h->in_slot.load()) return fail(h, RTC_ESTATE, "the handle's job is in a server slot");
+    if (const int busy = handle_busy(h)) return busy;
     if (!params || n != RTC_MLP_NPARAMS || !(sigma > 0.f) || !isfinite(sigma))
         return fail(h, RTC_EINVAL, "need RTC_MLP_NPARAMS parameters and sigma > 0");
     if (h->cfg.n_wfs != 1) return fail(h, RTC_EINVAL, "the predictor is for single-WFS handles");
@@ -719,7 +730,7 @@ int rtc_load_predictor(rtc_handle* h, const float* params, int64_t n, float sigm
 
 int rtc_set_predictor(rtc_handle* h, int32_t on) {
     if (!h) return RTC_EINVAL;
-    if (h->in_slot.load()) return fail(h, RTC_ESTATE, "the handle's job is in a server slot");
+    if (const int busy = handle_busy(h)) return busy;
     if (on && !h->pred) return fail(h, RTC_ESTATE, "no predictor loaded");
     h->pred_on = on != 0;
     return RTC_OK;
@@ -727,7 +738,7 @@ int rtc_set_predictor(rtc_handle* h, int32_t on) {
 
 int rtc_get_dm(rtc_handle* h, float* out) {
     if (!h || !out) return h ? fail(h, RTC_EINVAL, "out is NULL") : RTC_EINVAL;
-    if (h->in_slot.load()) return fail(h, RTC_ESTATE, "the handle's job is in a server slot");
+    if (const int busy = handle_busy(h)) return busy;
     DeviceScope ds(h->cfg.device);
     RTC_CUDA(h, cudaMemcpyAsync(out, h->d_a, h->cfg.nact * sizeof(float), cudaMemcpyDeviceToHost, h->stream));
     RTC_CUDA(h, cudaStreamSynchronize(h->stream));
@@ -762,8 +773,17 @@ int rtc_process_frame(rtc_handle* h, const uint16_t* frame, float* dm_out, float
     RTC_HOST_STAMP(0);
     int rc = check_ready(h);
     if (rc != RTC_OK) return rc;
-    if (h->in_slot.load()) return fail(h, RTC_ESTATE, "the handle's job is in a server slot");
     if (!frame || !dm_out) return fail(h, RTC_EINVAL, "frame and dm_out must be non-NULL");
+    if (h->resident) {
+        // the resident kernel takes the frame: pinned buffers only, no slopes
+        const uint16_t* d_frame = static_cast<const uint16_t*>(mapped_view(frame));
+        float* d_dm = static_cast<float*>(mapped_view(dm_out));
+        if (!d_frame || !d_dm || slopes_out)
+            return fail(h, RTC_ESTATE, "a resident handle takes pinned frame and dm buffers and no slopes_out");
+        DeviceScope ds(h->cfg.device);
+        return resident_frame(h, d_frame, d_dm);
+    }
+    if (const int busy = handle_busy(h)) return busy;
     DeviceScope ds(h->cfg.device);
     // pinned (page-locked, mapped) host buffers: the kernel reads the frame and writes
     // the commands over the host link, no copies and no stream synchronisation
@@ -811,7 +831,7 @@ int rtc_process_frame_async(rtc_handle* h, const uint16_t* d_frame, float* d_dm_
                             float* d_slopes_out, void* stream) {
     int rc = check_ready(h);
     if (rc != RTC_OK) return rc;
-    if (h->in_slot.load()) return fail(h, RTC_ESTATE, "the handle's job is in a server slot");
+    if (const int busy = handle_busy(h)) return busy;
     if (!d_frame) return fail(h, RTC_EINVAL, "d_frame is NULL");
     if (reinterpret_cast<uintptr_t>(d_frame) & 15) return fail(h, RTC_EINVAL, "d_frame must be 16-byte aligned");
     DeviceScope ds(h->cfg.device);
@@ -821,7 +841,7 @@ int rtc_process_frame_async(rtc_handle* h, const uint16_t* d_frame, float* d_dm_
 
 int rtc_centroid_async(rtc_handle* h, const uint16_t* d_frame, float* d_slopes_out, void* stream) {
     if (!h) return RTC_EINVAL;
-    if (h->in_slot.load()) return fail(h, RTC_ESTATE, "the handle's job is in a server slot");
+    if (const int busy = handle_busy(h)) return busy;
     if (!h->calib_loaded) return fail(h, RTC_ESTATE, "calibration maps not loaded");
     if (!d_frame) return fail(h, RTC_EINVAL, "d_frame is NULL");
     if (reinterpret_cast<uintptr_t>(d_frame) & 15) return fail(h, RTC_EINVAL, "d_frame must be 16-byte aligned");
@@ -836,7 +856,7 @@ int rtc_centroid_async(rtc_handle* h, const uint16_t* d_frame, float* d_slopes_o
 
 int rtc_reconstruct_async(rtc_handle* h, const float* d_slopes, float* d_dm_out, void* stream) {
     if (!h) return RTC_EINVAL;
-    if (h->in_slot.load()) return fail(h, RTC_ESTATE, "the handle's job is in a server slot");
+    if (const int busy = handle_busy(h)) return busy;
     if (h->store < 0) return fail(h, RTC_ESTATE, "control matrix not loaded");
     DeviceScope ds(h->cfg.device);
     cudaStream_t st = stream ? static_cast<cudaStream_t>(stream) : h->stream;
@@ -849,6 +869,7 @@ int rtc_reconstruct_async(rtc_handle* h, const float* d_slopes, float* d_dm_out,
 
 int rtc_synchronize(rtc_handle* h, void* stream) {
     if (!h) return RTC_EINVAL;
+    if (h->resident) return fail(h, RTC_ESTATE, "the handle is resident (rtc_resident_stop first)");
     DeviceScope ds(h->cfg.device);
     cudaStream_t st = stream ? static_cast<cudaStream_t>(stream) : h->stream;
     RTC_CUDA(h, cudaStreamSynchronize(st));

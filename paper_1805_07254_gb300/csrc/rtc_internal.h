@@ -54,6 +54,7 @@ struct LoopLaunch {
     const uint16_t* d_frames;
     unsigned long long frame_elems;
     const unsigned long long* d_seq;
+    const unsigned long long* d_ptrs;   // [nslot][2] frame and DM device views, or null (ring)
     float* d_dm;
     rtc_loop_done* d_done;
     unsigned long long n_frames;
@@ -122,6 +123,10 @@ struct rtc_handle {
     unsigned long long* h_seq = nullptr;      // pinned mapped [RTC_LOOP_SLOTS]
     float* h_dm_ring = nullptr;               // pinned mapped [RTC_LOOP_SLOTS][nact]
     rtc_loop_done* h_done = nullptr;          // pinned mapped [RTC_LOOP_SLOTS]
+    unsigned long long* h_ptrs = nullptr;     // pinned mapped [RTC_LOOP_SLOTS][2]: resident frame/DM views
+    bool resident = false;                    // rtc_resident_start .. rtc_resident_stop
+    unsigned long long res_k = 0;             // frames the present resident kernel has finished
+    int res_head0 = 0;                        // predictor ring head when it was launched
     int sbuf_kpad = -1;                       // kpad d_sbuf was sized for
 
     std::atomic<bool> in_slot{false};         // owned by a server slot (rtc_slot_submit)
@@ -209,6 +214,14 @@ bool rtc_handle_ready(const rtc_handle* h);
 // Device memory the handle holds (matrix, calibration, state, staging).
 int64_t rtc_handle_device_bytes(const rtc_handle* h);
 int fail_handle(rtc_handle* h, int code, const char* msg);
+
+// Resident mode (rtc_loop.cu): one frame through the resident kernel (pinned
+// buffers, device views); stop the kernel (rtc_resident_stop's body).
+int resident_frame(rtc_handle* h, const uint16_t* d_frame, float* d_dm);
+int resident_stop(rtc_handle* h);
+// RTC_ESTATE (with the reason recorded) if the handle's device work is owned by a
+// server slot or a resident kernel, else RTC_OK.
+int handle_busy(rtc_handle* h);
 
 // Host planning (plan.cu).  plan_slices: first subaperture of each slice (then
 // the subaperture count): equal slices, or with n_bands > 1 the asymmetric cut

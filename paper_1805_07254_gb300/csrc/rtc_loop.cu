@@ -100,7 +100,7 @@ int ensure_buffers(rtc_handle* h) {
 
 extern "C" int rtc_run_loop(rtc_handle* h, const rtc_loop_config* cfg, rtc_stats* stats) {
     if (!h) return RTC_EINVAL;
-    if (h->in_slot.load()) return fail_handle(h, RTC_ESTATE, "the handle's job is in a server slot");
+    if (const int busy = handle_busy(h)) return busy;
     if (!cfg || !stats) return fail_handle(h, RTC_EINVAL, "cfg and stats must be non-NULL");
     if (!h->calib_loaded || h->store < 0)
         return fail_handle(h, RTC_ESTATE, "calibration maps and control matrix must be loaded");
@@ -266,4 +266,168 @@ extern "C" int rtc_run_loop(rtc_handle* h, const rtc_loop_config* cfg, rtc_stats
     if (st != RTC_OK) return st;
     if (result != RTC_OK) return fail_handle(h, result, "a loop frame did not complete in time");
     return RTC_OK;
+}
+
+// ---- resident per-frame calls ---------------------------------------------------
+// The loop kernel launched for an unbounded run of frames; rtc_process_frame then
+// publishes one frame per call into slot k % RTC_LOOP_SLOTS, with the device views
+// of the caller's frame and DM buffers in the slot's pointer pair, and waits for
+// the slot's completion record.  Calls are synchronous, so a slot is free again
+// by the time it comes round.
+
+namespace {
+
+constexpr unsigned long long kResidentFrames = ~0ull >> 1;   // "until stopped"
+constexpr long long kResidentCheckNs = 20ll * 1000 * 1000;   // look at the kernel after 20 ms
+
+// The status word of an ended resident kernel, cleared.  A kernel whose frame wait
+// expired (the caller was idle) reports RTC_ETIMEDOUT, which is not an error here.
+int resident_status(rtc_handle* h, int& code) {
+    LOOP_CUDA(cudaMemcpyAsync(h->h_status, h->d_status, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    LOOP_CUDA(cudaMemsetAsync(h->d_status, 0, sizeof(int), h->stream));
+    LOOP_CUDA(cudaMemsetAsync(h->d_gridbar, 0, sizeof(unsigned long long), h->stream));
+    LOOP_CUDA(cudaStreamSynchronize(h->stream));
+    h->grid_epoch = 0;
+    code = *h->h_status;
+    // every frame the kernel finished pushed one measured vector into the history ring
+    if (h->pred_on) h->ring_head = static_cast<int>((h->res_head0 + h->res_k) & 3);
+    h->res_k = 0;
+    return RTC_OK;
+}
+
+int resident_launch(rtc_handle* h) {
+    for (int i = 0; i < RTC_LOOP_SLOTS; ++i) {
+        h->h_seq[i] = 0;
+        memset(&h->h_done[i], 0, sizeof(rtc_loop_done));
+    }
+    LOOP_CUDA(cudaMemsetAsync(h->d_gridbar, 0, sizeof(unsigned long long), h->stream));
+    LOOP_CUDA(cudaMemsetAsync(h->d_donectr, 0, sizeof(unsigned long long), h->stream));
+    LOOP_CUDA(cudaMemsetAsync(h->d_tseen, 0, 2 * sizeof(unsigned long long), h->stream));
+    h->grid_epoch = 0;
+    LoopLaunch ll{};
+    LOOP_CUDA(cudaHostGetDevicePointer(reinterpret_cast<void**>(const_cast<uint16_t**>(&ll.d_frames)), h->h_ring, 0));
+    LOOP_CUDA(cudaHostGetDevicePointer(reinterpret_cast<void**>(const_cast<unsigned long long**>(&ll.d_seq)), h->h_seq, 0));
+    LOOP_CUDA(cudaHostGetDevicePointer(reinterpret_cast<void**>(const_cast<unsigned long long**>(&ll.d_ptrs)), h->h_ptrs, 0));
+    LOOP_CUDA(cudaHostGetDevicePointer(reinterpret_cast<void**>(&ll.d_dm), h->h_dm_ring, 0));
+    LOOP_CUDA(cudaHostGetDevicePointer(reinterpret_cast<void**>(&ll.d_done), h->h_done, 0));
+    ll.frame_elems = static_cast<size_t>(h->cfg.n_wfs) * h->side * h->side;
+    ll.n_frames = kResidentFrames;
+    ll.nslot = RTC_LOOP_SLOTS;
+    ll.n_bands = 1;
+    ll.l2_stream = 0;
+    h->res_k = 0;
+    h->res_head0 = h->ring_head;
+    LOOP_CUDA(launch_loop(h, ll, h->stream));
+    return RTC_OK;
+}
+
+}  // namespace
+
+extern "C" int rtc_resident_start(rtc_handle* h) {
+    if (!h) return RTC_EINVAL;
+    if (h->in_slot.load()) return fail_handle(h, RTC_ESTATE, "the handle's job is in a server slot");
+    if (h->resident) return fail_handle(h, RTC_ESTATE, "the handle is already resident");
+    if (!h->calib_loaded || h->store < 0)
+        return fail_handle(h, RTC_ESTATE, "calibration maps and control matrix must be loaded");
+    if (h->kpad == 0) return fail_handle(h, RTC_ESTATE, "the resident kernel needs at least one valid subaperture");
+    int dev_prev = -1;
+    cudaGetDevice(&dev_prev);
+    if (dev_prev != h->cfg.device) cudaSetDevice(h->cfg.device);
+    struct Restore {
+        int d;
+        ~Restore() {
+            int cur = -1;
+            if (d >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != d) cudaSetDevice(d);
+        }
+    } restore{dev_prev};
+    int rc = ensure_buffers(h);
+    if (rc != RTC_OK) return rc;
+    if (!h->h_ptrs) {
+        LOOP_CUDA(cudaHostAlloc(reinterpret_cast<void**>(&h->h_ptrs),
+                                2 * RTC_LOOP_SLOTS * sizeof(unsigned long long), cudaHostAllocMapped));
+        memset(h->h_ptrs, 0, 2 * RTC_LOOP_SLOTS * sizeof(unsigned long long));
+    }
+    LOOP_CUDA(cudaStreamSynchronize(h->stream));
+    loop_begin();                       // releases of any handle wait for rtc_resident_stop
+    rc = resident_launch(h);
+    if (rc != RTC_OK) {
+        loop_end();
+        return rc;
+    }
+    h->resident = true;
+    return RTC_OK;
+}
+
+int resident_frame(rtc_handle* h, const uint16_t* d_frame, float* d_dm) {
+    if (reinterpret_cast<uintptr_t>(d_frame) % 16 != 0 || reinterpret_cast<uintptr_t>(d_dm) % 4 != 0)
+        return fail_handle(h, RTC_EINVAL, "resident mode: the frame buffer must be 16-byte aligned, dm_out 4-byte");
+    for (int attempt = 0; attempt < 2; ++attempt) {
+        // a kernel whose frame wait expired while the caller was idle has ended:
+        // launch it again (a grid barrier that expired is an error)
+        if (cudaStreamQuery(h->stream) != cudaErrorNotReady) {
+            int code = RTC_OK;
+            int rc = resident_status(h, code);
+            if (rc != RTC_OK) return rc;
+            if (code != RTC_OK && code != RTC_ETIMEDOUT)
+                return fail_handle(h, code, "the resident kernel ended with an error");
+            rc = resident_launch(h);
+            if (rc != RTC_OK) return rc;
+        }
+        const unsigned long long k = h->res_k;
+        const int slot = static_cast<int>(k % RTC_LOOP_SLOTS);
+        h->h_ptrs[2 * slot] = reinterpret_cast<uintptr_t>(d_frame);
+        h->h_ptrs[2 * slot + 1] = reinterpret_cast<uintptr_t>(d_dm);
+        store_release(&h->h_seq[slot], k + 1);
+        const long long t0 = mono_ns();
+        bool ended = false;
+        while (load_acquire(&h->h_done[slot].seq) != k + 1) {
+            const long long dt = mono_ns() - t0;
+            if (dt > kResidentCheckNs && cudaStreamQuery(h->stream) != cudaErrorNotReady) {
+                ended = load_acquire(&h->h_done[slot].seq) != k + 1;
+                break;
+            }
+            if (dt > kHostWaitNs) {
+                // the kernel neither finished the frame nor ended: stop it
+                store_release(&h->h_seq[slot], kStop);
+                cudaStreamSynchronize(h->stream);
+                int code = RTC_OK;
+                resident_status(h, code);
+                return fail_handle(h, RTC_ETIMEDOUT, "the resident kernel did not finish the frame in time");
+            }
+        }
+        if (!ended) {
+            h->res_k = k + 1;
+            return RTC_OK;
+        }
+        // the kernel ended (its frame wait expired) just before this frame was seen:
+        // relaunch and publish it again
+    }
+    return fail_handle(h, RTC_EDEVICE, "the resident kernel could not be restarted");
+}
+
+int resident_stop(rtc_handle* h) {
+    if (!h->resident) return RTC_OK;
+    if (cudaStreamQuery(h->stream) == cudaErrorNotReady)
+        store_release(&h->h_seq[h->res_k % RTC_LOOP_SLOTS], kStop);
+    const cudaError_t e = cudaStreamSynchronize(h->stream);
+    h->resident = false;
+    loop_end();
+    if (e != cudaSuccess) return fail_handle(h, RTC_EDEVICE, cudaGetErrorString(e));
+    int code = RTC_OK;
+    const int rc = resident_status(h, code);
+    if (rc != RTC_OK) return rc;
+    if (code != RTC_OK && code != RTC_ETIMEDOUT)
+        return fail_handle(h, code, "the resident kernel ended with an error");
+    return RTC_OK;
+}
+
+extern "C" int rtc_resident_stop(rtc_handle* h) {
+    if (!h) return RTC_EINVAL;
+    int dev_prev = -1;
+    cudaGetDevice(&dev_prev);
+    if (dev_prev != h->cfg.device) cudaSetDevice(h->cfg.device);
+    const int rc = resident_stop(h);
+    int cur = -1;
+    if (dev_prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != dev_prev) cudaSetDevice(dev_prev);
+    return rc;
 }

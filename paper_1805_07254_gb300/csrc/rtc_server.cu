@@ -127,6 +127,7 @@ int rtc_slot_submit(rtc_server* s, rtc_handle* h, const uint16_t* frames, uint64
     if (!rtc_handle_ready(h)) return sfail(RTC_ESTATE, "handle has no calibration or matrix");
     std::lock_guard<std::mutex> lock(s->mu);
     if (h->in_slot) return sfail(RTC_ESTATE, "handle is already in a slot");
+    if (h->resident) return sfail(RTC_ESTATE, "handle is resident (rtc_resident_stop first)");
     int free_slot = -1;
     for (int i = 0; i < s->max_slots; ++i)
         if (!s->jobs[i].active) {

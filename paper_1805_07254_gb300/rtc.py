@@ -83,6 +83,8 @@ SIGNATURES = {
     "rtc_mvm_integrate_noalloc": (_I, [_P, C.c_int32, _P, C.c_int32, C.c_int32, _P, _P, _P,
                                        C.c_float, C.c_float, C.c_int32, _P]),
     "rtc_run_loop": (_I, [_P, C.POINTER(RtcLoopConfig), C.POINTER(RtcStats)]),
+    "rtc_resident_start": (_I, [_P]),
+    "rtc_resident_stop": (_I, [_P]),
     "rtc_server_create": (_I, [C.c_int32, C.c_int32, C.c_int64, C.POINTER(_P)]),
     "rtc_server_destroy": (_I, [_P]),
     "rtc_slot_submit": (_I, [_P, _P, _P, C.c_uint64, _P, C.POINTER(C.c_int32)]),
@@ -260,6 +262,14 @@ class Rtc:
         return out
 
     # -- per frame -----------------------------------------------------------------
+    def resident_start(self):
+        """Keep the persistent kernel resident: process_frame on pinned buffers then
+        hands each frame to it without a launch (rtc_resident_start)."""
+        self._check(self._lib.rtc_resident_start(self._h))
+
+    def resident_stop(self):
+        self._check(self._lib.rtc_resident_stop(self._h))
+
     def process_frame(self, frame, dm_out=None, slopes_out=None, want_slopes: bool = False):
         """One synchronous step with host buffers.  ``frame`` is a uint16 numpy array or a
         (pinned) CPU tensor; returns dm (and slopes if requested)."""
