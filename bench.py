@@ -309,6 +309,24 @@ def launch_floor(torch, flush, st, n_steps, n_warm=20):
     return pct([a.elapsed_time(b) * 1e3 for a, b in evs], 0.5)
 
 
+def e2e_entry(s_launch, s_res, resident_headline, info, cfg, n, step_in_bytes, l2_bytes):
+    """The e2e object: rtc_process_frame with pinned host buffers, synchronous, host
+    clock.  Two modes of the same call: one kernel launch per call (L2 flushed before
+    each call) and the resident kernel (rtc_resident_start; no flush possible).  The
+    resident figure is the headline when the step's inputs exceed L2."""
+    launch = {"p50_us": round(s_launch["p50"], 3), "p99_us": round(s_launch["p99"], 3),
+              "rms_jitter_us": round(s_launch["rms_jitter"], 3), "l2": "flushed before each call"}
+    res = {"p50_us": round(s_res["p50"], 3), "p99_us": round(s_res["p99"], 3),
+           "rms_jitter_us": round(s_res["rms_jitter"], 3),
+           "l2": f"not flushed (step inputs {step_in_bytes / 1e6:.1f} MB against L2 {l2_bytes / 1e6:.1f} MB)"}
+    head = s_res if resident_headline else s_launch
+    return {"value": round(head["p50"], 3), "unit": "us", "p99_us": round(head["p99"], 3),
+            "rms_jitter_us": round(head["rms_jitter"], 3),
+            "mode": "resident kernel" if resident_headline else "one launch per call",
+            "h2d_bytes_per_step": info["frame_bytes"], "d2h_bytes_per_step": 4 * cfg.nact,
+            "steps": n, "launch_per_call": launch, "resident": res}
+
+
 def matrix_l2_label(matrix_bytes, forced_stream):
     """How the loop's matrix stream meets L2: "resident" (at most 80 MB with the default
     policy: it stays in L2 from frame to frame), or "streamed" (evict_first)."""
@@ -425,6 +443,26 @@ def ours(args):
         if i >= args.warmup:
             e2e_us.append((t1 - t0) / 1e3)
     s_e2e = stats_us(e2e_us)
+
+    # the same call with the persistent kernel resident (rtc_resident_start): no kernel
+    # launch per frame.  Nothing else may run on the GPU meanwhile, so there is no L2
+    # flush between these calls; they are the headline e2e only when the step's inputs
+    # are larger than L2 (the FP32 frame: 144.8 MB), as the timing rule requires
+    r.resident_start()
+    res_us = []
+    try:
+        for i in range(args.warmup + n_e2e):
+            t0 = time.perf_counter_ns()
+            r.process_frame(pin_frames[i % n_frames], dm_out=pin_dm)
+            t1 = time.perf_counter_ns()
+            if i >= args.warmup:
+                res_us.append((t1 - t0) / 1e3)
+    finally:
+        r.resident_stop()
+    s_res = stats_us(res_us)
+    step_in_bytes = info["matrix_bytes"] + info["frame_bytes"] + info["calib_bytes"]
+    l2_bytes = int(getattr(torch.cuda.get_device_properties(dev), "L2_cache_size", 0) or (126 << 20))
+    resident_headline = step_in_bytes > l2_bytes
 
     variants = {}
     if not args.no_variants:
@@ -581,10 +619,7 @@ def ours(args):
                      "frac": round(frame_gbs / hbm_peak, 4), "traffic": traffic,
                      "algorithmic_bytes": step_bytes,
                      "launch_floor_us": round(floor_us, 3)},
-        "e2e": {"value": round(s_e2e["p50"], 3), "unit": "us", "p99_us": round(s_e2e["p99"], 3),
-                "rms_jitter_us": round(s_e2e["rms_jitter"], 3),
-                "h2d_bytes_per_step": info["frame_bytes"], "d2h_bytes_per_step": 4 * cfg.nact,
-                "steps": n_e2e},
+        "e2e": e2e_entry(s_e2e, s_res, resident_headline, info, cfg, n_e2e, step_in_bytes, l2_bytes),
         "gpu_launches": args.steps,
         "clocks": clocks,
         "timed_wall_s_incl_flush": round(t_wall, 3),

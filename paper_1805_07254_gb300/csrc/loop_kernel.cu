@@ -76,6 +76,16 @@ using rtc_pixel::kUnitRegs;
 constexpr unsigned long long kFrameWaitNs = 2000ull * 1000 * 1000;   // 2 s for a frame to arrive
 constexpr unsigned long long kStop = ~0ull;
 
+#ifndef RTC_LOOP_POLLERS
+#define RTC_LOOP_POLLERS 1
+#endif
+// Warps whose lane 0 polls host memory for the frame, their first polls spread over
+// about one round trip.  One per block: four (to see a publication sooner) made the
+// host-measured latency 6 us worse, the extra system-scope polls slowing the host's
+// own publication and completion reads.
+constexpr int kPollers = RTC_LOOP_POLLERS;
+constexpr unsigned long long kPollSpreadNs = 1200;
+
 struct LoopArgs {
     rtc_pixel::PixelArgs px;           // frame and s are set per frame
     Args mv;                           // s and dm_out are set per frame
@@ -121,7 +131,7 @@ template <int DT, int NPX, bool PRED>
 __global__ void __launch_bounds__(kThreads, 1) loop_kernel(LoopArgs L) {
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ Shared sh;
-    __shared__ int stop_now;
+    __shared__ int poll_state;               // this frame: 0 waiting, 1 published, 2 stop
     __shared__ const uint16_t* frame_in;     // this frame's pixels (ring slot or caller's buffer)
     __shared__ float* dm_to;                 // where this frame's DM commands go
     const int tid = threadIdx.x;
@@ -132,6 +142,7 @@ __global__ void __launch_bounds__(kThreads, 1) loop_kernel(LoopArgs L) {
     if (tid == 0) {
         init_shared(sh);
         pl = make_plan(L.mv, smem);
+        poll_state = 0;
     }
     __syncthreads();
 
@@ -155,6 +166,8 @@ __global__ void __launch_bounds__(kThreads, 1) loop_kernel(LoopArgs L) {
     const int npp = L.px.npx * L.px.npx;
     const long long cal_lines = (static_cast<long long>(pl.g1 - pl.g0) * npp * 4 + 127) / 128;
     const int slot_lane = 2 * (tid >> 5) + ((tid >> 4) & 1);
+    // the grid position of the thread's first subaperture: the same every frame
+    const int2 pos0 = rtc_pixel::subap_pos(L.px, pl.g0 + slot_lane, pl.g0 + slot_lane < pl.g1);
     constexpr unsigned long long kBarriers = PRED ? 2 : 1;     // grid barriers per frame
     int tile = 0;
     for (unsigned long long k = 0; k < L.n_frames; ++k) {
@@ -175,39 +188,52 @@ __global__ void __launch_bounds__(kThreads, 1) loop_kernel(LoopArgs L) {
             const int f = bk.x + tid + j * kConsumers;
             ur[j] = f < bk.y ? __ldg(L.units + f) : kNoUnit;
         }
-        // 1. wait for the band of frame k that completes the block's subapertures
-        if (tid == 0) {
-            int stop = 0;
+        // 1. wait for the band of frame k that completes the block's subapertures:
+        //    the pollers' first loads are staggered; whichever sees the band first
+        //    (an acquire) reads the frame's buffers and tells the others
+        if ((tid & 31) == 0 && (tid >> 5) < kPollers) {
+            volatile int* state = &poll_state;
             const unsigned long long want = k * static_cast<unsigned long long>(L.n_bands) + bk.z + 1;
             const unsigned long long t0 = global_ns();
-            unsigned long long t = t0;
-            while (true) {
+            const unsigned long long delay = (tid >> 5) * kPollSpreadNs / kPollers;
+            while (*state == 0 && global_ns() - t0 < delay) {
+            }
+            while (*state == 0) {
                 const unsigned long long v = ld_acquire_sys(L.seq + slot);
-                t = global_ns();
+                const unsigned long long t = global_ns();
                 if (v == kStop) {
-                    stop = 1;
+                    *state = 2;
                     break;
                 }
-                if (v >= want) break;
+                if (v >= want) {
+                    // the frame's buffers: written by the host before it published the frame
+                    const uint16_t* fr = L.frames + static_cast<size_t>(slot) * L.frame_elems;
+                    float* dm = L.dm_ring + static_cast<size_t>(slot) * L.mv.nact;
+                    if (L.ptrs) {
+                        fr = reinterpret_cast<const uint16_t*>(ld_relaxed_sys(L.ptrs + 2 * slot));
+                        dm = reinterpret_cast<float*>(ld_relaxed_sys(L.ptrs + 2 * slot + 1));
+                    }
+                    frame_in = fr;
+                    dm_to = dm;
+                    atomicMax(L.t_seen + (k & 1), t);
+                    *state = 1;
+                    break;
+                }
                 if (t - t0 > kFrameWaitNs) {
                     atomicExch(L.mv.status, RTC_ETIMEDOUT);
-                    stop = 1;
+                    *state = 2;
                     break;
                 }
-            }
-            if (!stop) atomicMax(L.t_seen + (k & 1), t);
-            if (stop) sh.abort_flag = 1;            // the producer stops too
-            stop_now = stop;
-            // the frame's buffers: written by the host before it published the frame
-            frame_in = L.frames + static_cast<size_t>(slot) * L.frame_elems;
-            dm_to = L.dm_ring + static_cast<size_t>(slot) * L.mv.nact;
-            if (L.ptrs && !stop) {
-                frame_in = reinterpret_cast<const uint16_t*>(ld_relaxed_sys(L.ptrs + 2 * slot));
-                dm_to = reinterpret_cast<float*>(ld_relaxed_sys(L.ptrs + 2 * slot + 1));
             }
         }
         consumer_sync();
-        if (stop_now) break;
+        if (poll_state == 2) {
+            if (tid == 0) sh.abort_flag = 1;        // the producer stops too
+            break;
+        }
+        // every thread has read the state (a late reader may see the reset: it only
+        // tests for a stop), and the next frame's pollers start after later barriers
+        if (tid == 0) poll_state = 0;
         RTC_LOOP_STAMP(0);
 
         // 2. the block's pixels into device memory, then the block's slopes from
@@ -228,8 +254,9 @@ __global__ void __launch_bounds__(kThreads, 1) loop_kernel(LoopArgs L) {
         for (int base = pl.g0; base < pl.g1; base += 2 * kConsumerWarps) {
             const int gi = base + slot_lane;
             const bool valid = gi < pl.g1;
-            const float2 sxy = rtc_pixel::subap_slopes<NPX, rtc_pixel::kPixelL2, 16>(
-                L.px, L.stage, s_k, gi, valid, tid & 31);
+            const int2 pos = base == pl.g0 ? pos0 : rtc_pixel::subap_pos(L.px, gi, valid);
+            const float2 sxy = rtc_pixel::subap_slopes_at<NPX, rtc_pixel::kPixelL2, 16>(
+                L.px, L.stage, s_k, gi, valid, tid & 31, pos);
             if (valid && (tid & 15) == 0) {
                 int ix, iy;
                 local_index(L.mv, pl, gi, ix, iy);
