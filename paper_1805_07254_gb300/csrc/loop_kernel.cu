@@ -84,6 +84,11 @@ constexpr unsigned long long kStop = ~0ull;
 // host-measured latency 6 us worse, the extra system-scope polls slowing the host's
 // own publication and completion reads.
 constexpr int kPollers = RTC_LOOP_POLLERS;
+#ifndef RTC_HOST_POLL_STRIDE
+#define RTC_HOST_POLL_STRIDE 8
+#endif
+// With whole frames, one block in this many polls host memory for the frame.
+constexpr int kHostPollStride = RTC_HOST_POLL_STRIDE;
 constexpr unsigned long long kPollSpreadNs = 1200;
 
 struct LoopArgs {
@@ -99,6 +104,10 @@ struct LoopArgs {
     const unsigned long long* seq;     // mapped host [nslot]: bands published
     const unsigned long long* ptrs;    // mapped host [nslot][2] or null: the frame's own
                                        // frame and DM buffers (device views; resident mode)
+    int host_poll_stride;              // blocks b with b % stride == 0 poll host memory; the
+                                       // others poll the device mirror (whole frames only)
+    unsigned long long* mirror;        // device [nslot]: highest published value seen
+    unsigned long long* mirror_ptrs;   // device [nslot][2]: the frame's buffers, copied
     float* dm_ring;                    // mapped host [nslot][nact]
     rtc_loop_done* done;               // mapped host [nslot]
     float* s_buf;                      // device [2][kpad]
@@ -122,6 +131,19 @@ __device__ __forceinline__ unsigned long long ld_relaxed_sys(const unsigned long
     unsigned long long v;
     asm volatile("ld.relaxed.sys.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
     return v;
+}
+__device__ __forceinline__ unsigned long long ld_acquire_gpu(const unsigned long long* p) {
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ unsigned long long ld_relaxed_gpu(const unsigned long long* p) {
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void red_release_gpu_max(unsigned long long* p, unsigned long long v) {
+    asm volatile("red.release.gpu.global.max.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 __device__ __forceinline__ void st_release_sys(unsigned long long* p, unsigned long long v) {
     asm volatile("st.release.sys.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
@@ -190,18 +212,25 @@ __global__ void __launch_bounds__(kThreads, 1) loop_kernel(LoopArgs L) {
         }
         // 1. wait for the band of frame k that completes the block's subapertures:
         //    the pollers' first loads are staggered; whichever sees the band first
-        //    (an acquire) reads the frame's buffers and tells the others
+        //    (an acquire) reads the frame's buffers and tells the others.  With whole
+        //    frames only every host_poll_stride-th block polls host memory; it copies
+        //    what it saw into a device mirror (a release), which the other blocks
+        //    poll in L2, so that the host link carries a few polls instead of one per
+        //    block
         if ((tid & 31) == 0 && (tid >> 5) < kPollers) {
             volatile int* state = &poll_state;
             const unsigned long long want = k * static_cast<unsigned long long>(L.n_bands) + bk.z + 1;
+            const bool host = blockIdx.x % L.host_poll_stride == 0;
+            const bool mirrored = L.host_poll_stride > 1;
             const unsigned long long t0 = global_ns();
             const unsigned long long delay = (tid >> 5) * kPollSpreadNs / kPollers;
             while (*state == 0 && global_ns() - t0 < delay) {
             }
             while (*state == 0) {
-                const unsigned long long v = ld_acquire_sys(L.seq + slot);
+                const unsigned long long v = host ? ld_acquire_sys(L.seq + slot) : ld_acquire_gpu(L.mirror + slot);
                 const unsigned long long t = global_ns();
                 if (v == kStop) {
+                    if (host && mirrored) red_release_gpu_max(L.mirror + slot, v);
                     *state = 2;
                     break;
                 }
@@ -210,9 +239,18 @@ __global__ void __launch_bounds__(kThreads, 1) loop_kernel(LoopArgs L) {
                     const uint16_t* fr = L.frames + static_cast<size_t>(slot) * L.frame_elems;
                     float* dm = L.dm_ring + static_cast<size_t>(slot) * L.mv.nact;
                     if (L.ptrs) {
-                        fr = reinterpret_cast<const uint16_t*>(ld_relaxed_sys(L.ptrs + 2 * slot));
-                        dm = reinterpret_cast<float*>(ld_relaxed_sys(L.ptrs + 2 * slot + 1));
+                        const unsigned long long* src = host ? L.ptrs : L.mirror_ptrs;
+                        const unsigned long long a = host ? ld_relaxed_sys(src + 2 * slot) : ld_relaxed_gpu(src + 2 * slot);
+                        const unsigned long long b =
+                            host ? ld_relaxed_sys(src + 2 * slot + 1) : ld_relaxed_gpu(src + 2 * slot + 1);
+                        fr = reinterpret_cast<const uint16_t*>(a);
+                        dm = reinterpret_cast<float*>(b);
+                        if (host && mirrored) {
+                            L.mirror_ptrs[2 * slot] = a;
+                            L.mirror_ptrs[2 * slot + 1] = b;
+                        }
                     }
+                    if (host && mirrored) red_release_gpu_max(L.mirror + slot, v);
                     frame_in = fr;
                     dm_to = dm;
                     atomicMax(L.t_seen + (k & 1), t);
@@ -391,6 +429,9 @@ cudaError_t launch_dt(rtc_handle* h, const LoopLaunch& ll, cudaStream_t st) {
     a.n_bands = ll.n_bands;
     a.seq = ll.d_seq;
     a.ptrs = ll.d_ptrs;
+    a.host_poll_stride = ll.n_bands == 1 ? kHostPollStride : 1;
+    a.mirror = h->d_mirror;
+    a.mirror_ptrs = h->d_mirror + RTC_LOOP_SLOTS;
     a.dm_ring = ll.d_dm;
     a.done = ll.d_done;
     a.s_buf = h->d_sbuf;

@@ -476,6 +476,7 @@ int rtc_destroy(rtc_handle* h) {
     free_dev(h->d_gridbar);
     free_dev(h->d_sbuf);
     free_dev(h->d_donectr);
+    free_dev(h->d_mirror);
     free_dev(h->d_tseen);
     free_dev(h->d_units);
     free_dev(h->d_blk);

@@ -124,6 +124,8 @@ struct rtc_handle {
     float* h_dm_ring = nullptr;               // pinned mapped [RTC_LOOP_SLOTS][nact]
     rtc_loop_done* h_done = nullptr;          // pinned mapped [RTC_LOOP_SLOTS]
     unsigned long long* h_ptrs = nullptr;     // pinned mapped [RTC_LOOP_SLOTS][2]: resident frame/DM views
+    unsigned long long* d_mirror = nullptr;   // device [RTC_LOOP_SLOTS] + [RTC_LOOP_SLOTS][2]: the loop's
+                                              // device copy of the published flags and buffers
     bool resident = false;                    // rtc_resident_start .. rtc_resident_stop
     unsigned long long res_k = 0;             // frames the present resident kernel has finished
     int res_head0 = 0;                        // predictor ring head when it was launched

@@ -84,6 +84,7 @@ int ensure_buffers(rtc_handle* h) {
         LOOP_CUDA(cudaHostAlloc(reinterpret_cast<void**>(&h->h_done),
                                 RTC_LOOP_SLOTS * sizeof(rtc_loop_done), cudaHostAllocMapped));
         LOOP_CUDA(cudaMalloc(&h->d_donectr, sizeof(unsigned long long)));
+        LOOP_CUDA(cudaMalloc(&h->d_mirror, 3 * RTC_LOOP_SLOTS * sizeof(unsigned long long)));
         LOOP_CUDA(cudaMalloc(&h->d_tseen, 2 * sizeof(unsigned long long)));
     }
     if (h->sbuf_kpad != h->kpad) {
@@ -149,6 +150,7 @@ extern "C" int rtc_run_loop(rtc_handle* h, const rtc_loop_config* cfg, rtc_stats
             memcpy(h->h_ring + i * frame_elems, cfg->preload + i * frame_elems, frame_elems * 2);
     LOOP_CUDA(cudaMemsetAsync(h->d_gridbar, 0, sizeof(unsigned long long), h->stream));
     LOOP_CUDA(cudaMemsetAsync(h->d_donectr, 0, sizeof(unsigned long long), h->stream));
+    LOOP_CUDA(cudaMemsetAsync(h->d_mirror, 0, 3 * RTC_LOOP_SLOTS * sizeof(unsigned long long), h->stream));
     LOOP_CUDA(cudaMemsetAsync(h->d_tseen, 0, 2 * sizeof(unsigned long long), h->stream));
     h->grid_epoch = 0;
 
@@ -302,6 +304,7 @@ int resident_launch(rtc_handle* h) {
     }
     LOOP_CUDA(cudaMemsetAsync(h->d_gridbar, 0, sizeof(unsigned long long), h->stream));
     LOOP_CUDA(cudaMemsetAsync(h->d_donectr, 0, sizeof(unsigned long long), h->stream));
+    LOOP_CUDA(cudaMemsetAsync(h->d_mirror, 0, 3 * RTC_LOOP_SLOTS * sizeof(unsigned long long), h->stream));
     LOOP_CUDA(cudaMemsetAsync(h->d_tseen, 0, 2 * sizeof(unsigned long long), h->stream));
     h->grid_epoch = 0;
     LoopLaunch ll{};
