@@ -159,3 +159,65 @@ def test_destroy_stops_a_resident_handle():
     r2, *_ = make_pair(cfg)
     r2.process_frame(pin[0], dm_out=dm)
     r2.close()
+
+
+def test_six_wfs_and_asymmetric_cut_resident_equal_the_launch_path():
+    """Several WFS in one frame, and a handle re-cut for a banded readout (its frames
+    still handed over whole): the resident frames are the launch path's bit for bit."""
+    cfg = synth.elt_scao_6wfs()
+    frames, _ = synth.make_frames(cfg, 0, 2)
+    pin = _pinned(frames.numpy())
+    r1, *_ = make_pair(cfg, store="fp8")
+    r2, *_ = make_pair(cfg, store="fp8")
+    ref = _launch_path(r2, pin, 3, cfg.nact)
+    dm = torch.empty(cfg.nact).pin_memory()
+    r1.resident_start()
+    try:
+        for k in range(3):
+            r1.process_frame(pin[k % 2], dm_out=dm)
+            np.testing.assert_array_equal(dm.numpy(), ref[k])
+    finally:
+        r1.resident_stop()
+    r1.close()
+    r2.close()
+
+    cfg = synth.elt_scao()
+    frames, _ = synth.make_frames(cfg, 0, 2)
+    pin = _pinned(frames.numpy())
+    r1, *_ = make_pair(cfg)
+    r2, *_ = make_pair(cfg)
+    for r in (r1, r2):
+        r.set_readout(74, 10.0)
+    ref = _launch_path(r2, pin, 3, cfg.nact)
+    r1.resident_start()
+    try:
+        for k in range(3):
+            r1.process_frame(pin[k % 2], dm_out=dm)
+            np.testing.assert_array_equal(dm.numpy(), ref[k])
+    finally:
+        r1.resident_stop()
+
+
+def test_server_refuses_a_resident_handle_and_stop_after_an_idle_expiry():
+    from paper_1805_07254_gb300 import Server
+    cfg = synth.tiny_scao()
+    frames, _ = synth.make_frames(cfg, 0, 2)
+    pin = _pinned(frames.numpy())
+    r, *_ = make_pair(cfg)
+    srv = Server(max_slots=2)
+    r.resident_start()
+    try:
+        with pytest.raises(RtcError) as e:
+            srv.submit(r, frames.numpy())
+        assert e.value.code == RTC_ESTATE
+        # a pinned frame with a pageable DM buffer is refused too
+        with pytest.raises(RtcError) as e:
+            r.process_frame(pin[0], dm_out=np.empty(cfg.nact, np.float32))
+        assert e.value.code == RTC_ESTATE
+        time.sleep(2.6)                   # the kernel's frame wait expires meanwhile
+    finally:
+        r.resident_stop()                 # stopping an already ended kernel is fine
+    dm = torch.empty(cfg.nact).pin_memory()
+    r.process_frame(pin[0], dm_out=dm)    # the launch path works again
+    srv.close()
+    r.close()
