@@ -80,9 +80,8 @@ constexpr unsigned long long kStop = ~0ull;
 #define RTC_LOOP_POLLERS 1
 #endif
 // Warps whose lane 0 polls host memory for the frame, their first polls spread over
-// about one round trip.  One per block: four (to see a publication sooner) made the
-// host-measured latency 6 us worse, the extra system-scope polls slowing the host's
-// own publication and completion reads.
+// about one round trip.  One per polling block: four (to see a publication sooner)
+// measured 6 us worse host to host.
 constexpr int kPollers = RTC_LOOP_POLLERS;
 #ifndef RTC_HOST_POLL_STRIDE
 #define RTC_HOST_POLL_STRIDE 8
